@@ -1,0 +1,339 @@
+/*
+ * lem_oracle.c -- serial FP64 restatement of the landscape-evolution step of
+ * Barnes, "Accelerating a Landscape Evolution Model with Parallelism"
+ * (arXiv:1803.02977), Section "The Algorithm", Algorithms 1-6.
+ *
+ * TEST INFRASTRUCTURE ONLY: the plain reference the CUDA library is checked
+ * against.  Written for a reader to verify against the paper by eye; no
+ * blocking, fusion or reordering beyond what the algorithms state.
+ * Compile with -O2 -ffp-contract=off (no fused multiply-add, no fast-math).
+ */
+#include "lem_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Double nearest 1/sqrt(2) and sqrt(2); both are decimal literals so that
+ * the value does not depend on a library's sqrt. */
+static const double ORC_INV_SQRT2 = 0.70710678118654752440;
+static const double ORC_SQRT2 = 1.41421356237309504880;
+
+/* Offsets (dx, dy) of the eight neighbours in ascending address order. */
+static const int ORC_DX[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+static const int ORC_DY[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+
+static int orc_is_diagonal(int k) { return ORC_DX[k] != 0 && ORC_DY[k] != 0; }
+
+static int orc_on_perimeter(int nx, int ny, int x, int y) {
+  return x == 0 || y == 0 || x == nx - 1 || y == ny - 1;
+}
+
+/* ---- Alg 1: Determine Receivers ------------------------------------------ */
+
+static void orc_receivers_impl(int nx, int ny, const double* h, const float* hf,
+                               int32_t* rec) {
+  /* Initialise Rec to NoFlow (self) -- this covers the perimeter. */
+  for (int64_t c = 0; c < (int64_t)nx * ny; ++c) rec[c] = (int32_t)c;
+  for (int y = 1; y < ny - 1; ++y) {
+    for (int x = 1; x < nx - 1; ++x) {
+      int64_t c = (int64_t)y * nx + x;
+      double hc = h ? h[c] : (double)hf[c];
+      double smax = 0.0;     /* maximum slope so far */
+      int64_t nmax = c;      /* neighbour with that slope (NoFlow = self) */
+      for (int k = 0; k < 8; ++k) {
+        int64_t n = (int64_t)(y + ORC_DY[k]) * nx + (x + ORC_DX[k]);
+        double hn = h ? h[n] : (double)hf[n];
+        double w = orc_is_diagonal(k) ? ORC_INV_SQRT2 : 1.0;
+        double s = (hc - hn) * w;  /* slope from c to n, times dx */
+        if (s > smax) {
+          smax = s;
+          nmax = n;
+        }
+      }
+      rec[c] = (int32_t)nmax;
+    }
+  }
+}
+
+void orc_receivers(int nx, int ny, const double* h, int32_t* rec) {
+  orc_receivers_impl(nx, ny, h, NULL, rec);
+}
+
+void orc_receivers_f32(int nx, int ny, const float* h, int32_t* rec) {
+  orc_receivers_impl(nx, ny, NULL, h, rec);
+}
+
+/* ---- Alg 2: Determine Donors --------------------------------------------- */
+
+void orc_donors_grid(int nx, int ny, const int32_t* rec, int32_t* dnum, int32_t* donor) {
+  for (int y = 0; y < ny; ++y) {
+    for (int x = 0; x < nx; ++x) {
+      int64_t c = (int64_t)y * nx + x;
+      dnum[c] = 0;
+      for (int k = 0; k < 8; ++k) {
+        int xn = x + ORC_DX[k], yn = y + ORC_DY[k];
+        if (xn < 0 || yn < 0 || xn >= nx || yn >= ny) continue;
+        int64_t n = (int64_t)yn * nx + xn;
+        if (rec[n] == c) {
+          donor[8 * c + dnum[c]] = (int32_t)n;
+          dnum[c] = dnum[c] + 1;
+        }
+      }
+    }
+  }
+}
+
+int orc_donors_graph(int n, const int32_t* rec, int dmax, int32_t* dnum, int32_t* donor) {
+  for (int c = 0; c < n; ++c) {
+    dnum[c] = 0;
+    for (int v = 0; v < n; ++v) {
+      if (v != c && rec[v] == c) {
+        if (dnum[c] >= dmax) return -1;
+        donor[(int64_t)dmax * c + dnum[c]] = v;
+        dnum[c] = dnum[c] + 1;
+      }
+    }
+  }
+  return 0;
+}
+
+/* ---- Alg 3: Generate Queue (breadth first) ------------------------------- */
+
+int64_t orc_queue(int64_t n, const int32_t* rec, int dmax, const int32_t* dnum,
+                  const int32_t* donor, int32_t* queue, int64_t* levels, int32_t* depth) {
+  int64_t nqueue = 0;  /* open location in Queue */
+  int64_t ls = 0;      /* write location in Levels */
+  for (int64_t c = 0; c < n; ++c) depth[c] = -1;
+
+  levels[ls++] = 0;
+  /* Source cells: every cell without a receiver. */
+  for (int64_t c = 0; c < n; ++c) {
+    if (rec[c] == c) {
+      queue[nqueue++] = (int32_t)c;
+      depth[c] = 0;
+    }
+  }
+  if (nqueue == 0) return 0;
+  levels[ls++] = nqueue;
+
+  /* Expand level by level: the donors of the cells of level l form l+1. */
+  int64_t lo = 0, hi = nqueue;
+  int32_t l = 0;
+  while (lo < hi) {
+    for (int64_t i = lo; i < hi; ++i) {
+      int32_t c = queue[i];
+      for (int k = 0; k < dnum[c]; ++k) {
+        int32_t d = donor[(int64_t)dmax * c + k];
+        queue[nqueue++] = d;
+        depth[d] = l + 1;
+      }
+    }
+    lo = hi;
+    hi = nqueue;
+    if (hi > lo) levels[ls++] = nqueue;  /* close the non-empty level */
+    l = l + 1;
+  }
+  return ls - 1;
+}
+
+/* ---- Alg 4: Flow Accumulation (Eq. 2, w = 1) ----------------------------- */
+
+void orc_accumulate(int64_t n, const int32_t* queue, const int64_t* levels, int64_t nlevels,
+                    int dmax, const int32_t* dnum, const int32_t* donor, int64_t* cnt) {
+  for (int64_t c = 0; c < n; ++c) cnt[c] = 1;
+  for (int64_t l = nlevels - 2; l >= 0; --l) {
+    for (int64_t i = levels[l]; i < levels[l + 1]; ++i) {
+      int32_t c = queue[i];
+      for (int k = 0; k < dnum[c]; ++k) {
+        int32_t d = donor[(int64_t)dmax * c + k];
+        cnt[c] = cnt[c] + cnt[d];
+      }
+    }
+  }
+}
+
+/* ---- Alg 5: Uplift -------------------------------------------------------- */
+
+void orc_uplift(int nx, int ny, double* h, const orc_params* p) {
+  for (int y = 1; y < ny - 1; ++y) {
+    for (int x = 1; x < nx - 1; ++x) {
+      int64_t c = (int64_t)y * nx + x;
+      double u = p->Ufield ? p->Ufield[c] : p->U;
+      h[c] = h[c] + u * p->dt;
+    }
+  }
+}
+
+/* ---- Alg 6: Calculate Erosion -------------------------------------------- */
+
+/* dist(c, r) for a receiver r adjacent to c. */
+static double orc_dist(int nx, int32_t c, int32_t r, double dx) {
+  int64_t dxi = (int64_t)(r % nx) - (int64_t)(c % nx);
+  int64_t dyi = (int64_t)(r / nx) - (int64_t)(c / nx);
+  return (dxi != 0 && dyi != 0) ? dx * ORC_SQRT2 : dx;
+}
+
+void orc_erode(int nx, int ny, double* h, const int32_t* rec, const int32_t* queue,
+               const int64_t* levels, int64_t nlevels, const int64_t* cnt, const orc_params* p) {
+  (void)ny;
+  for (int64_t l = 1; l < nlevels; ++l) {
+    for (int64_t i = levels[l]; i < levels[l + 1]; ++i) {
+      int32_t c = queue[i];           /* focal cell */
+      int32_t r = rec[c];             /* its receiver */
+      double A = (double)cnt[c] * p->area_scale;
+      double F = p->K * p->dt * pow(A, p->m) / orc_dist(nx, c, r, p->dx);
+      double h0 = h[c];
+      double hr = h[r];
+      h[c] = (h0 + F * hr) / (1.0 + F);
+    }
+  }
+}
+
+void orc_erode_newton(int nx, int ny, double* h, const int32_t* rec, const int32_t* queue,
+                      const int64_t* levels, int64_t nlevels, const int64_t* cnt,
+                      const orc_params* p, double n_exp, double eps, int max_iter) {
+  (void)ny;
+  for (int64_t l = 1; l < nlevels; ++l) {
+    for (int64_t i = levels[l]; i < levels[l + 1]; ++i) {
+      int32_t c = queue[i];
+      int32_t r = rec[c];
+      double A = (double)cnt[c] * p->area_scale;
+      double F = p->K * p->dt * pow(A, p->m) / pow(orc_dist(nx, c, r, p->dx), n_exp);
+      double h0 = h[c];
+      double hn = h[r];
+      double hnew = h0;      /* current updated value */
+      double hp = h0;        /* previous updated value */
+      double delta = 2.0 * eps;
+      int it = 0;
+      while (fabs(delta) > eps && it < max_iter) {
+        double f = hnew - h0 + F * pow(hnew - hn, n_exp);
+        double fp = 1.0 + F * n_exp * pow(hnew - hn, n_exp - 1.0);
+        hnew = hnew - f / fp;
+        delta = hnew - hp;
+        hp = hnew;
+        ++it;
+      }
+      h[c] = hnew;
+    }
+  }
+}
+
+/* ---- Rinse, Repeat -------------------------------------------------------- */
+
+int orc_run(int nx, int ny, double* h, int nsteps, const orc_params* p,
+            const int32_t* frozen_rec, int64_t* nlevels_out) {
+  int64_t n = (int64_t)nx * ny;
+  int32_t* rec = (int32_t*)malloc(sizeof(int32_t) * n);
+  int32_t* dnum = (int32_t*)malloc(sizeof(int32_t) * n);
+  int32_t* donor = (int32_t*)malloc(sizeof(int32_t) * 8 * n);
+  int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * n);
+  int32_t* depth = (int32_t*)malloc(sizeof(int32_t) * n);
+  int64_t* levels = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * n);
+  int rc = 0;
+  if (!rec || !dnum || !donor || !queue || !depth || !levels || !cnt) {
+    rc = -1;
+    goto done;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    if (frozen_rec)
+      memcpy(rec, frozen_rec, sizeof(int32_t) * n);
+    else
+      orc_receivers(nx, ny, h, rec);
+    orc_donors_grid(nx, ny, rec, dnum, donor);
+    int64_t L = orc_queue(n, rec, 8, dnum, donor, queue, levels, depth);
+    orc_accumulate(n, queue, levels, L, 8, dnum, donor, cnt);
+    orc_uplift(nx, ny, h, p);
+    orc_erode(nx, ny, h, rec, queue, levels, L, cnt, p);
+    if (nlevels_out) nlevels_out[s] = L;
+  }
+done:
+  free(rec);
+  free(dnum);
+  free(donor);
+  free(queue);
+  free(depth);
+  free(levels);
+  free(cnt);
+  return rc;
+}
+
+/* ---- Adjoint and tangent-linear of one n-hat = 1 step ---------------------- */
+
+/* F and dF/dK = dt*A^m/d of the eroding cell c. */
+static void orc_F(int nx, int32_t c, int32_t r, int64_t count, const orc_params* p,
+                  double* F, double* G) {
+  double A = (double)count * p->area_scale;
+  double d = orc_dist(nx, c, r, p->dx);
+  *F = p->K * p->dt * pow(A, p->m) / d;
+  *G = p->dt * pow(A, p->m) / d;
+}
+
+void orc_tangent_step(int nx, int ny, const double* h_next, const int32_t* rec,
+                      const int32_t* queue, const int64_t* levels, int64_t nlevels,
+                      const int64_t* cnt, const orc_params* p, const double* dh,
+                      const double* dU, double dK, double* dh_next) {
+  /* Level 0: perimeter cells keep h; interior pits take uplift only. */
+  for (int64_t i = levels[0]; i < levels[1]; ++i) {
+    int32_t c = queue[i];
+    int x = c % nx, y = c / nx;
+    if (orc_on_perimeter(nx, ny, x, y))
+      dh_next[c] = dh[c];
+    else
+      dh_next[c] = dh[c] + p->dt * dU[c];
+  }
+  /* Levels 1.., receivers first:
+   * (1+F) dh'_c = dh_c + dt dU_c + F dh'_r + dF (h'_r - h'_c),  dF = G dK. */
+  for (int64_t l = 1; l < nlevels; ++l) {
+    for (int64_t i = levels[l]; i < levels[l + 1]; ++i) {
+      int32_t c = queue[i];
+      int32_t r = rec[c];
+      double F, G;
+      orc_F(nx, c, r, cnt[c], p, &F, &G);
+      double num = dh[c] + p->dt * dU[c] + F * dh_next[r] + G * dK * (h_next[r] - h_next[c]);
+      dh_next[c] = num / (1.0 + F);
+    }
+  }
+}
+
+void orc_adjoint_step(int nx, int ny, const double* h_next, const int32_t* rec,
+                      const int32_t* queue, const int64_t* levels, int64_t nlevels,
+                      const int64_t* cnt, const orc_params* p, const double* lam,
+                      double* lam_prev, double* dLdU, double* dLdK) {
+  int64_t n = (int64_t)nx * ny;
+  double* mu = (double*)malloc(sizeof(double) * n);
+  if (!mu) return;
+  for (int64_t c = 0; c < n; ++c) mu[c] = lam[c];
+  /* Transpose of the receivers-first sweep: donors first (levels high to 1),
+   * each eroding cell passing mu_c * F_c/(1+F_c) to its receiver. */
+  for (int64_t l = nlevels - 1; l >= 1; --l) {
+    for (int64_t i = levels[l]; i < levels[l + 1]; ++i) {
+      int32_t c = queue[i];
+      int32_t r = rec[c];
+      double F, G;
+      orc_F(nx, c, r, cnt[c], p, &F, &G);
+      mu[r] = mu[r] + mu[c] * (F / (1.0 + F));
+    }
+  }
+  double gK = 0.0;
+  for (int64_t l = 1; l < nlevels; ++l) {
+    for (int64_t i = levels[l]; i < levels[l + 1]; ++i) {
+      int32_t c = queue[i];
+      int32_t r = rec[c];
+      double F, G;
+      orc_F(nx, c, r, cnt[c], p, &F, &G);
+      lam_prev[c] = mu[c] / (1.0 + F);
+      dLdU[c] = dLdU[c] + p->dt * mu[c] / (1.0 + F);
+      gK = gK + mu[c] * G * (h_next[r] - h_next[c]) / (1.0 + F);
+    }
+  }
+  for (int64_t i = levels[0]; i < levels[1]; ++i) {
+    int32_t c = queue[i];
+    int x = c % nx, y = c / nx;
+    lam_prev[c] = mu[c];
+    if (!orc_on_perimeter(nx, ny, x, y)) dLdU[c] = dLdU[c] + p->dt * mu[c];
+  }
+  *dLdK = *dLdK + gK;
+  free(mu);
+}
