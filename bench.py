@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Throughput of the landscape-evolution time step on GB300, in cell-steps/s.
+
+A step is one full time step of the method (receivers, donors, levels,
+accumulation, uplift + erosion) over the whole synthetic grid.  Default
+workload: 2048 x 2048 FP64 grid, seeded [0,1) noise plus a 1e-4 south tilt,
+dx = 100 m, K = 1e-5 /yr, m = 0.5, U = 1e-3 m/yr, dt = 1000 yr.
+
+The working set of that grid (~72 MB) fits in the 129 MB L2, so every timed
+step is bracketed by CUDA events on the launching stream and the L2 is
+flushed (a 512 MiB write) between timed steps, outside the events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Under torchrun each rank advances its own replica of the grid (one grid does
+not shard: its level order is global); the reported value is the sum over
+ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "cell-steps/s"
+# algorithmic bytes per cell-step by phase (elevation bytes P, count bytes Ab):
+#   receivers+donors P+2 (read h, write receiver code and donor mask),
+#   levels 10 (mask, frontier read, queue write, sink scan),
+#   accumulate 5+2Ab (queue, mask, donor counts, count write),
+#   erode 5+Ab+3P (queue, receiver code, count, h_c, h_r, h write)
+PHASES = ("receivers", "levels", "accumulate", "erode")
+
+
+def algo_bytes(P, Ab):
+    return {"receivers": P + 2, "levels": 10, "accumulate": 5 + 2 * Ab, "erode": 5 + Ab + 3 * P}
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="grid2048_f64")
+    ap.add_argument("--flush-mib", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-phases", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_params(w):
+    import oracle
+    return oracle.params(dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt)
+
+
+def cpu_oracle_rate(w, target_s, h0=None):
+    """Time the oracle (single thread, as written) on the workload's own
+    initial surface; scale the step count so the sample takes ~target_s."""
+    import oracle
+    p = oracle_params(w)
+    h0 = w.initial() if h0 is None else h0
+    side = w.nx
+    # one probe step on the full grid decides the sample size
+    t0 = time.perf_counter()
+    oracle.run(h0, p, 1)
+    t1 = time.perf_counter() - t0
+    if t1 * 2 > target_s:
+        # full-grid steps are too slow: run a smaller square of the same recipe
+        from paper_1803_02977_gb300 import synth
+        frac = max(1e-3, target_s / (4 * t1))
+        side = max(64, int(w.nx * frac ** 0.5))
+        h0 = synth.noise_surface(side, side, w.seed, 0.0, w.noise_hi, w.south_tilt, w.dx)
+        t0 = time.perf_counter()
+        oracle.run(h0, p, 1)
+        t1 = time.perf_counter() - t0
+    nsteps = max(1, int(target_s / max(t1, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.run(h0, p, nsteps)
+    el = time.perf_counter() - t0
+    cells = h0.size
+    return {"value": cells * nsteps / el, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{nsteps} oracle steps on a {h0.shape[1]}x{h0.shape[0]} grid of the "
+                      f"same recipe, {el:.1f} s, single-threaded C (-O2, FP64)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1803_02977_gb300 import synth
+    import oracle
+    w = synth.workload(args.workload)
+    p = oracle_params(w)
+    h = w.initial()
+    # size each step so that warmup + steps end within a few minutes
+    t0 = time.perf_counter()
+    oracle.run(h, p, 1)
+    t1 = time.perf_counter() - t0
+    budget = 150.0
+    if t1 * (args.steps + args.warmup) > budget:
+        frac = budget / (t1 * (args.steps + args.warmup))
+        side = max(32, int(w.nx * frac ** 0.5))
+        h = synth.noise_surface(side, side, w.seed, 0.0, w.noise_hi, w.south_tilt, w.dx)
+        sample = f"each step: one oracle step on a {side}x{side} grid of the same recipe"
+    else:
+        sample = f"each step: one oracle step on the full {w.nx}x{w.ny} grid"
+    h = oracle.run(h, p, args.warmup)
+    t0 = time.perf_counter()
+    oracle.run(h, p, args.steps)
+    el = time.perf_counter() - t0
+    cells = h.size
+    value = cells * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, args),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(w, args):
+    return {"workload": w.name, "nx": w.nx, "ny": w.ny, "dtype": w.dtype,
+            "count_bits": 64 if w.area_dtype == "i64" else 32, "dx": w.dx, "K": w.K, "m": w.m,
+            "U": w.U, "dt": w.dt, "seed": w.seed, "noise": [0.0, w.noise_hi],
+            "south_tilt": w.south_tilt, "area_scale": "dx*dx",
+            "l2": f"flushed between timed steps ({args.flush_mib} MiB write)",
+            "parallelism": f"replicas{args.gpus}"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1803_02977_gb300 import lem, synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.workload(args.workload)
+    tdtype = torch.float64 if w.dtype == "f64" else torch.float32
+    P = 8 if w.dtype == "f64" else 4
+    Ab = 8 if w.area_dtype == "i64" else 4
+    count_bits = 8 * Ab
+    h0_np = w.initial().astype(np.float64 if P == 8 else np.float32)
+    N = w.nx * w.ny
+    par = dict(dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt, count_bits=count_bits)
+
+    h = torch.tensor(h0_np, device=dev)
+    mdl = lem.Model(h, **par)
+    flush = torch.empty(args.flush_mib << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        mdl.step(1)
+        flush.zero_()
+    mdl.sync()
+
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_wall = time.perf_counter()
+    for i in range(K):
+        ev0[i].record(stream)
+        mdl.step(1)
+        ev1[i].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    barrier()
+    clk = clocks.stop()
+    mdl.sync()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    tot_ms = float(sum(step_ms))
+    t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tot_ms = float(t.item())
+    value = N * K * ws / (tot_ms / 1e3)
+    ms_per_step = tot_ms / K
+
+    # level count of the state reached (outside the timed region)
+    mdl.receivers()
+    L = lem.lem_levels(mdl.ctx)
+
+    # per-phase split through the stage-by-stage calls (outside the timed region)
+    phases = None
+    if not args.no_phases:
+        hp = torch.tensor(h0_np, device=dev)
+        mp = lem.Model(hp, **par)
+        reps = 5
+        acc = {k: 0.0 for k in PHASES}
+        for r in range(reps + 1):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(PHASES) + 1)]
+            flush.zero_()
+            evs[0].record(stream)
+            mp.receivers()
+            evs[1].record(stream)
+            lem.lem_levels(mp.ctx)
+            evs[2].record(stream)
+            lem.lem_accumulate(mp.ctx)
+            evs[3].record(stream)
+            mp.erode()
+            evs[4].record(stream)
+            torch.cuda.synchronize()
+            if r > 0:
+                for i, k in enumerate(PHASES):
+                    acc[k] += evs[i].elapsed_time(evs[i + 1]) / reps
+        ab = algo_bytes(P, Ab)
+        peak = measured_peaks().get("hbm_gbs")
+        phases = {k: {"ms": acc[k], "algo_bytes_per_cell": ab[k],
+                      "gbs": ab[k] * N / (acc[k] / 1e3) / 1e9,
+                      "cell_steps_per_s": N / (acc[k] / 1e3)} for k in PHASES}
+        if peak:
+            for k in PHASES:
+                phases[k]["frac_of_measured_hbm"] = phases[k]["gbs"] / peak
+        mp.close()
+
+    # end to end through the public API: pinned host h -> device, one step,
+    # device -> pinned host, every step
+    hh = torch.tensor(h0_np).pin_memory()
+    hd = torch.empty_like(hh, device=dev)
+    me = lem.Model(hd, **par)
+    Ke = max(3, min(K, 20))
+    for _ in range(2):
+        hd.copy_(hh, non_blocking=True)
+        me.step(1)
+        hh.copy_(hd, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(Ke):
+        hd.copy_(hh, non_blocking=True)
+        me.step(1)
+        hh.copy_(hd, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    me.sync()
+    e2e_ms = e0.elapsed_time(e1)
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = N * Ke * ws / (float(te.item()) / 1e3)
+    me.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(w, args.cpu_seconds)
+
+    peaks = measured_peaks()
+    ab = algo_bytes(P, Ab)
+    per_cell = sum(ab.values())
+    achieved = per_cell * N / (ms_per_step / 1e3) / 1e9
+    peak = peaks.get("hbm_gbs")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if peak else None, "traffic": None,
+                "kernel": "lem_step_kernel (one cooperative launch per step)",
+                "algo_bytes_per_cell_step": per_cell,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peak else None}
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
+            "config": config_of(w, args), "levels_after": int(L),
+            "step_ms_min_median_max": [min(step_ms), float(np.median(step_ms)), max(step_ms)],
+            "wall_s_timed_region": t_wall,
+            "roofline": roofline, "phases": phases, "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": N * P,
+                    "d2h_bytes_per_step": N * P, "steps": Ke},
+            "gpu_launches": K, "cpu_baseline": cpu}
+    mdl.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

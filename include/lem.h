@@ -1,0 +1,181 @@
+/*
+ * lem.h -- C ABI of the GB300 (sm_103a) landscape-evolution time step.
+ *
+ * Implements, on one GPU, the per-timestep method of Barnes, "Accelerating a
+ * Landscape Evolution Model with Parallelism" (arXiv:1803.02977), Section
+ * "The Algorithm": receivers (Alg 1), donors (Alg 2), the breadth-first
+ * queue of levels (Alg 3), flow accumulation (Alg 4, Eq. 2), uplift (Alg 5)
+ * and implicit stream-power erosion for n-hat = 1 (Alg 6, Eq. 1), repeated
+ * ("Rinse, Repeat").
+ *
+ * Conventions shared by every entry point
+ *  - Grid: width nx, height ny, cell (x, y) at address c = y*nx + x, rows
+ *    growing southward (Section "Step 1: Initialization").  Perimeter cells
+ *    are fixed base level and never have a receiver.
+ *  - Neighbour code k = 0..7 in ascending address order:
+ *      0=NW 1=N 2=NE 3=W 4=E 5=SW 6=S 7=SE.
+ *  - "No receiver" (NoFlow) is exported as rec[c] = c.
+ *  - Pointers named dev_* are CUDA device pointers owned by the caller;
+ *    the library never frees them.  Host pointers are named plainly.
+ *  - Every call is asynchronous on the context's stream except those that
+ *    return a host value computed on the device (lem_levels, lem_sync),
+ *    which synchronise that stream.
+ *  - Every call returns a status (LEM_OK or a negative LEM_E* code) and
+ *    never throws.  Errors found by a kernel (a receiver cycle, a timed-out
+ *    device wait) are sticky and reported by the next synchronising call.
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef LEM_H
+#define LEM_H
+
+#include <stdint.h>
+
+/* Symbols of the shared library are exported explicitly. */
+#if defined(__GNUC__)
+#define LEM_API __attribute__((visibility("default")))
+#else
+#define LEM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lem_ctx lem_ctx;
+
+/* Status codes. */
+enum {
+  LEM_OK = 0,
+  LEM_EINVAL = -1,    /* bad argument, or a frozen receiver graph with a cycle */
+  LEM_ENOMEM = -2,    /* device allocation failed                              */
+  LEM_ECUDA = -3,     /* a CUDA runtime call failed                            */
+  LEM_ETIMEOUT = -4,  /* a bounded device-side wait ran out                    */
+  LEM_ESTATE = -5,    /* a stage was called before its inputs were computed    */
+  LEM_EOVERFLOW = -6  /* grid too large for 32-bit cell addresses              */
+};
+
+/* Elevation element types. */
+enum { LEM_F64 = 0, LEM_F32 = 1 };
+
+/* Model parameters (Section "Step 1: Initialization"; Eq. 1 with n-hat = 1).
+ *  nx, ny      grid width and height, each >= 3, nx*ny < 2^31
+ *  dx          cell spacing in metres (dy = dx), > 0
+ *  K           erodibility, >= 0 (K = 0 leaves pure uplift)
+ *  m           area exponent m-hat, finite
+ *  U           uplift rate u-hat in m/yr, finite (Alg 5)
+ *  dt          time step in years, > 0
+ *  area_scale  drainage area per counted cell: A = count * area_scale in the
+ *              erosion factor; <= 0 selects dx*dx (Alg 4 initialises A to
+ *              dx*dy)
+ *  dtype       LEM_F64 or LEM_F32: element type of the bound elevations.
+ *              Receiver slopes are always compared in FP64.
+ *  count_bits  32 or 64: integer width of the cell counts (Alg 4). */
+typedef struct {
+  int nx, ny;
+  double dx, K, m, U, dt;
+  double area_scale;
+  int dtype;
+  int count_bits;
+} lem_params;
+
+/* Create a context for an nx-by-ny FP64 grid with 32-bit counts and
+ * area_scale = dx*dx.  Allocates the context's device scratch (about
+ * 15 bytes per cell plus a 1 MiB erosion table) on the current device.
+ * On failure *out is set to NULL. */
+LEM_API int lem_create(lem_ctx** out, int nx, int ny, double dx, double K, double m, double U,
+               double dt);
+
+/* Create a context from a full parameter set (see lem_params). */
+LEM_API int lem_create_ex(lem_ctx** out, const lem_params* p);
+
+/* Free the context and its device scratch.  NULL is ignored. */
+LEM_API void lem_destroy(lem_ctx* ctx);
+
+/* Issue all later work on `stream` (a cudaStream_t; NULL = legacy default). */
+LEM_API int lem_set_stream(lem_ctx* ctx, void* stream);
+
+/* Bind the caller's elevation array: nx*ny elements of `dtype` (which must
+ * match the context's), row-major, updated in place by lem_erode/lem_step.
+ * Binding invalidates every derived stage. */
+LEM_API int lem_bind_elevation(lem_ctx* ctx, void* dev_h, int dtype);
+
+/* Per-cell uplift rate (nx*ny doubles, m/yr) replacing the scalar U of
+ * Alg 5 (whose text notes spatially varying uplift stays trivially
+ * parallel); NULL restores the scalar. Perimeter entries are ignored. */
+LEM_API int lem_set_uplift_field(lem_ctx* ctx, const double* dev_U);
+
+/* Alg 1 (Step 2, Determine Receivers): for each interior cell, the
+ * neighbour of greatest strictly positive slope (h[c]-h[n])/dist, lowest k
+ * on ties, else NoFlow.  Slopes are compared as (h[c]-h[n])*w in FP64 with
+ * w = 1 (cardinal) or the double nearest 1/sqrt(2) (diagonal).  Also
+ * computes the donor masks of Alg 2.  If dev_rec is not NULL it receives
+ * nx*ny int32 receiver addresses (self = NoFlow).  On a frozen context
+ * (lem_set_receivers) the frozen graph is exported instead. */
+LEM_API int lem_receivers(lem_ctx* ctx, int32_t* dev_rec);
+
+/* Alg 2 (Step 3, Determine Donors), the inverse of the receivers, over every
+ * cell including the perimeter.  dev_dnum (nx*ny int32) receives the donor
+ * counts; dev_donor (8*nx*ny int32, Dmax = 8 per cell) receives the donor
+ * addresses of cell c at [8c, 8c+dnum[c]) in k order, the rest set to -1.
+ * Either pointer may be NULL.  Requires lem_receivers. */
+LEM_API int lem_donors(lem_ctx* ctx, int32_t* dev_dnum, int32_t* dev_donor);
+
+/* Alg 3 (Step 4, Generate Queue): breadth-first levels grown from the cells
+ * without receivers.  Level 0 lists those cells in ascending address order;
+ * level l+1 lists the donors of level l's cells, in queue order, each cell's
+ * donors in k order.  *nlevels receives L (synchronises the stream).
+ * Optional outputs: dev_queue (nx*ny int32), dev_levels (L+1 int64 offsets,
+ * levels[0] = 0, levels[L] = nx*ny; size the buffer nx*ny+1), dev_depth
+ * (nx*ny int32, the level of each cell).  Returns LEM_EINVAL if a frozen
+ * receiver graph leaves cells unreached (a cycle).  Requires lem_receivers. */
+LEM_API int lem_levels(lem_ctx* ctx, int64_t* nlevels, int32_t* dev_queue, int64_t* dev_levels,
+               int32_t* dev_depth);
+
+/* Alg 4 (Step 5, Flow Accumulation, Eq. 2 with w = 1): integer cell counts
+ * A(c) = 1 + sum of the donors' counts, swept from the highest level down.
+ * If dev_counts is not NULL it receives nx*ny counts of the context's
+ * count width (int32 or int64).  Requires lem_levels. */
+LEM_API int lem_accumulate(lem_ctx* ctx, void* dev_counts);
+
+/* Alg 5 + Alg 6 (Steps 6-7) for n-hat = 1, fused: interior cells without a
+ * receiver are uplifted, h += dt*U; then, level 1 upward, every cell takes
+ * h = (h + dt*U + F*h_r) / (1 + F), F = K*dt*(count*area_scale)^m / d,
+ * d = dx (cardinal receiver) or dx*sqrt(2) (diagonal), h_r the receiver's
+ * updated elevation.  FP32 contexts evaluate the same update in the
+ * increment form h0 - g*(h0 - h_r), g = F/(1+F) rounded once from FP64.
+ * Updates the bound elevations in place.  Requires lem_accumulate. */
+LEM_API int lem_erode(lem_ctx* ctx);
+
+/* "Rinse, Repeat": nsteps full time steps (receivers through erosion) in
+ * one cooperative persistent launch with device-wide barriers between
+ * levels; no host round trip between levels or steps. */
+LEM_API int lem_step(lem_ctx* ctx, int nsteps);
+
+/* Freeze the receiver graph: dev_rec (nx*ny int32, self = NoFlow, every
+ * other entry an in-grid neighbour, perimeter cells self) replaces Alg 1 in
+ * every later stage and step until called again with NULL.  The graph is
+ * copied.  Returns LEM_EINVAL for an out-of-range entry (checked on the
+ * device; reported by the next synchronising call). */
+LEM_API int lem_set_receivers(lem_ctx* ctx, const int32_t* dev_rec);
+
+/* Synchronise the context's stream and return the sticky device status
+ * (then cleared). */
+LEM_API int lem_sync(lem_ctx* ctx);
+
+/* Upper bound, in seconds, on every device-side wait (grid barriers);
+ * default 2 s.  A wait that runs out makes its kernel return early with
+ * LEM_ETIMEOUT recorded. */
+LEM_API int lem_set_wait_limit(lem_ctx* ctx, double seconds);
+
+/* Launch one kernel that waits, bounded by the wait limit, on a device flag
+ * that nothing sets; returns LEM_ETIMEOUT once the limit has run out and
+ * the context stays usable.  Exercises the timeout path without a fault. */
+LEM_API int lem_selftest_wait(lem_ctx* ctx);
+
+/* Static description of a status code. */
+LEM_API const char* lem_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEM_H */

@@ -1,0 +1,492 @@
+// lem_api.cu -- the C ABI declared in include/lem.h: context management,
+// argument and state checks, cooperative launches of the persistent step
+// kernel, and the small kernels that convert the internal compact arrays to
+// the paper's exported layouts (Table 1: Rec, Donor/Dnum, Queue, Levels,
+// Accum).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "lem.h"
+#include "lem_step_kernel.cuh"
+
+using namespace lem;
+
+struct lem_ctx {
+  lem_params p;
+  int N = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  void* h = nullptr;
+  const double* Uf = nullptr;
+  uint8_t* code = nullptr;
+  uint8_t* mask = nullptr;
+  int* queue = nullptr;
+  int* levels = nullptr;
+  void* cnt = nullptr;
+  double* Ftab = nullptr;
+  float* gtab = nullptr;
+  DevState* st = nullptr;
+  int* partial = nullptr;
+  int grid = 0;
+  int* host_status = nullptr;  // pinned: [err, nlevels]
+  bool rec_valid = false, lev_valid = false, acc_valid = false, frozen = false;
+  double Kdt = 0, dxd = 0, area_scale = 0;
+  double wait_limit_s = 2.0;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return LEM_OK;
+  if (e == cudaErrorMemoryAllocation) return LEM_ENOMEM;
+  return LEM_ECUDA;
+}
+
+#define LEM_CUDA(call)                        \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+__global__ void build_tables_kernel(double* Ftab, float* gtab, double Kdt, double m, double dx,
+                                    double dxd, double area_scale) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kTableN; i += gridDim.x * blockDim.x) {
+    const double A = __dmul_rn((double)i, area_scale);
+    const double P = __dmul_rn(Kdt, pow(A, m));
+    const double Fc = __ddiv_rn(P, dx);
+    const double Fd = __ddiv_rn(P, dxd);
+    Ftab[i] = Fc;
+    Ftab[kTableN + i] = Fd;
+    gtab[i] = (float)(Fc / (1.0 + Fc));
+    gtab[kTableN + i] = (float)(Fd / (1.0 + Fd));
+  }
+}
+
+__global__ void export_rec_kernel(const uint8_t* __restrict__ code, int32_t* __restrict__ rec,
+                                  int N, int nx) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+    const int k = code[c];
+    rec[c] = (k == kSink) ? c : c + nbr_off(k, nx);
+  }
+}
+
+__global__ void export_donors_kernel(const uint8_t* __restrict__ mask, int32_t* __restrict__ dnum,
+                                     int32_t* __restrict__ donor, int N, int nx) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+    int msk = mask[c];
+    if (dnum) dnum[c] = __popc(msk);
+    if (donor) {
+      int i = 0;
+      while (msk) {
+        const int k = __ffs(msk) - 1;
+        msk &= msk - 1;
+        donor[8LL * c + i++] = c + nbr_off(k, nx);
+      }
+      for (; i < 8; ++i) donor[8LL * c + i] = -1;
+    }
+  }
+}
+
+__global__ void export_levels_kernel(const int* __restrict__ levels, int64_t* __restrict__ out,
+                                     int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = levels[i];
+}
+
+__global__ void export_depth_kernel(const int* __restrict__ queue, const int* __restrict__ levels,
+                                    int L, int32_t* __restrict__ depth, int N) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+    int lo = 0, hi = L;  // find l with levels[l] <= j < levels[l+1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (levels[mid] <= j) lo = mid; else hi = mid;
+    }
+    depth[queue[j]] = lo;
+  }
+}
+
+// Frozen receivers: int32 addresses -> codes; invalid entries are an error.
+__global__ void import_rec_kernel(const int32_t* __restrict__ rec, uint8_t* __restrict__ code,
+                                  int N, int nx, int ny, DevState* st) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+    const int r = rec[c];
+    const int x = c % nx, y = c / nx;
+    const bool perim = (x == 0 || y == 0 || x == nx - 1 || y == ny - 1);
+    int k = kSink;
+    if (r != c) {
+      if (perim || r < 0 || r >= N) {
+        set_error(st, kErrInval);
+      } else {
+        const int ddx = r % nx - x, ddy = r / nx - y;
+        for (int q = 0; q < 8; ++q)
+          if (nbr_dx(q) == ddx && nbr_dy(q) == ddy) k = q;
+        if (k == kSink) set_error(st, kErrInval);
+      }
+    }
+    code[c] = (uint8_t)k;
+  }
+}
+
+// Waits on a flag nothing sets, bounded by the context's wait limit.
+__global__ void selftest_wait_kernel(DevState* st) {
+  if (threadIdx.x != 0) return;
+  const unsigned long long t0 = global_ns();
+  while (ld_volatile(&st->selftest_flag) == 0) {
+    if (global_ns() - t0 > st->wait_limit_ns) {
+      set_error(st, kErrTimeout);
+      return;
+    }
+  }
+}
+
+template <typename HT, typename CT>
+const void* step_kernel_ptr() {
+  return (const void*)&lem_step_kernel<HT, CT>;
+}
+
+const void* kernel_for(const lem_ctx* c) {
+  const bool f64 = c->p.dtype == LEM_F64, c64 = c->p.count_bits == 64;
+  if (f64) return c64 ? step_kernel_ptr<double, long long>() : step_kernel_ptr<double, int>();
+  return c64 ? step_kernel_ptr<float, long long>() : step_kernel_ptr<float, int>();
+}
+
+template <typename HT, typename CT>
+StepArgs<HT, CT> make_args(lem_ctx* c, int phases, int nsteps) {
+  StepArgs<HT, CT> a;
+  a.nx = c->p.nx;
+  a.ny = c->p.ny;
+  a.N = c->N;
+  a.h = (HT*)c->h;
+  a.Uf = c->Uf;
+  a.U = c->p.U;
+  a.dt = c->p.dt;
+  a.Kdt = c->Kdt;
+  a.m = c->p.m;
+  a.dx = c->p.dx;
+  a.dxd = c->dxd;
+  a.area_scale = c->area_scale;
+  a.code = c->code;
+  a.mask = c->mask;
+  a.queue = c->queue;
+  a.levels = c->levels;
+  a.cnt = (CT*)c->cnt;
+  a.Ftab = c->Ftab;
+  a.gtab = c->gtab;
+  a.st = c->st;
+  a.partial = c->partial;
+  a.phases = phases;
+  a.nsteps = nsteps;
+  a.frozen = c->frozen ? 1 : 0;
+  return a;
+}
+
+template <typename HT, typename CT>
+int launch_typed(lem_ctx* c, int phases, int nsteps) {
+  StepArgs<HT, CT> a = make_args<HT, CT>(c, phases, nsteps);
+  void* args[] = {&a};
+  LEM_CUDA(cudaLaunchCooperativeKernel(step_kernel_ptr<HT, CT>(), dim3(c->grid), dim3(kBD), args,
+                                       0, c->stream));
+  return LEM_OK;
+}
+
+int launch_step(lem_ctx* c, int phases, int nsteps) {
+  const bool f64 = c->p.dtype == LEM_F64, c64 = c->p.count_bits == 64;
+  if (f64) return c64 ? launch_typed<double, long long>(c, phases, nsteps)
+                      : launch_typed<double, int>(c, phases, nsteps);
+  return c64 ? launch_typed<float, long long>(c, phases, nsteps)
+             : launch_typed<float, int>(c, phases, nsteps);
+}
+
+int aux_grid(const lem_ctx* c) {
+  long long blocks = ((long long)c->N + 255) / 256;
+  return (int)(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096);
+}
+
+// Read the sticky status (and L) back; synchronises the stream.
+int read_status(lem_ctx* c, int* nlevels) {
+  LEM_CUDA(cudaMemcpyAsync(c->host_status, &c->st->err, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                           c->stream));
+  LEM_CUDA(cudaStreamSynchronize(c->stream));
+  const int err = c->host_status[0];
+  if (nlevels) *nlevels = c->host_status[1];
+  if (err != 0) {
+    // an abandoned barrier may have left arrivals counted: start clean
+    LEM_CUDA(cudaMemsetAsync(&c->st->bar_count, 0, sizeof(unsigned), c->stream));
+    LEM_CUDA(cudaMemsetAsync(&c->st->err, 0, sizeof(int), c->stream));
+    LEM_CUDA(cudaStreamSynchronize(c->stream));
+    return err;
+  }
+  return LEM_OK;
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+}  // namespace
+
+extern "C" {
+
+const char* lem_status_string(int s) {
+  switch (s) {
+    case LEM_OK: return "ok";
+    case LEM_EINVAL: return "invalid argument or receiver graph";
+    case LEM_ENOMEM: return "device allocation failed";
+    case LEM_ECUDA: return "CUDA runtime error";
+    case LEM_ETIMEOUT: return "bounded device wait ran out";
+    case LEM_ESTATE: return "stage called before its inputs were computed";
+    case LEM_EOVERFLOW: return "grid too large for 32-bit cell addresses";
+    default: return "unknown status";
+  }
+}
+
+int lem_create(lem_ctx** out, int nx, int ny, double dx, double K, double m, double U,
+               double dt) {
+  lem_params p;
+  std::memset(&p, 0, sizeof(p));
+  p.nx = nx;
+  p.ny = ny;
+  p.dx = dx;
+  p.K = K;
+  p.m = m;
+  p.U = U;
+  p.dt = dt;
+  p.area_scale = 0.0;
+  p.dtype = LEM_F64;
+  p.count_bits = 32;
+  return lem_create_ex(out, &p);
+}
+
+int lem_create_ex(lem_ctx** out, const lem_params* pin) {
+  if (!out) return LEM_EINVAL;
+  *out = nullptr;
+  if (!pin) return LEM_EINVAL;
+  const lem_params p = *pin;
+  if (p.nx < 3 || p.ny < 3) return LEM_EINVAL;
+  if ((long long)p.nx * p.ny >= (1LL << 31) - 2) return LEM_EOVERFLOW;
+  if (!is_finite(p.dx) || p.dx <= 0 || !is_finite(p.dt) || p.dt <= 0 || !is_finite(p.K) || p.K < 0 ||
+      !is_finite(p.m) || !is_finite(p.U) || !is_finite(p.area_scale))
+    return LEM_EINVAL;
+  if (p.dtype != LEM_F64 && p.dtype != LEM_F32) return LEM_EINVAL;
+  if (p.count_bits != 32 && p.count_bits != 64) return LEM_EINVAL;
+
+  lem_ctx* c = new (std::nothrow) lem_ctx();
+  if (!c) return LEM_ENOMEM;
+  c->p = p;
+  c->N = p.nx * p.ny;
+  c->Kdt = p.K * p.dt;
+  c->dxd = p.dx * kSqrt2;
+  c->area_scale = p.area_scale > 0 ? p.area_scale : p.dx * p.dx;
+  int rc = LEM_OK;
+  cudaError_t e = cudaGetDevice(&c->device);
+  const size_t N = (size_t)c->N;
+  int nsm = 0, per_sm = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(c), kBD, 0);
+  if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+  if (e == cudaSuccess) {
+    c->grid = nsm * (per_sm < 2 ? per_sm : 2);
+    e = cudaMalloc(&c->code, N);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&c->mask, N);
+  if (e == cudaSuccess) e = cudaMalloc(&c->queue, N * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->levels, (N + 2) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->cnt, N * (p.count_bits / 8));
+  if (e == cudaSuccess) e = cudaMalloc(&c->Ftab, 2 * kTableN * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->gtab, 2 * kTableN * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&c->st, sizeof(DevState));
+  if (e == cudaSuccess) e = cudaMalloc(&c->partial, (size_t)c->grid * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->host_status, 4 * sizeof(int));
+  if (e == cudaSuccess) {
+    DevState s;
+    std::memset(&s, 0, sizeof(s));
+    s.wait_limit_ns = (unsigned long long)(c->wait_limit_s * 1e9);
+    e = cudaMemcpy(c->st, &s, sizeof(s), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) {
+    build_tables_kernel<<<64, 256>>>(c->Ftab, c->gtab, c->Kdt, p.m, p.dx, c->dxd, c->area_scale);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    rc = cuda_status(e);
+    lem_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return LEM_OK;
+}
+
+void lem_destroy(lem_ctx* c) {
+  if (!c) return;
+  cudaFree(c->code);
+  cudaFree(c->mask);
+  cudaFree(c->queue);
+  cudaFree(c->levels);
+  cudaFree(c->cnt);
+  cudaFree(c->Ftab);
+  cudaFree(c->gtab);
+  cudaFree(c->st);
+  cudaFree(c->partial);
+  if (c->host_status) cudaFreeHost(c->host_status);
+  delete c;
+}
+
+int lem_set_stream(lem_ctx* c, void* stream) {
+  if (!c) return LEM_EINVAL;
+  c->stream = (cudaStream_t)stream;
+  return LEM_OK;
+}
+
+int lem_bind_elevation(lem_ctx* c, void* dev_h, int dtype) {
+  if (!c || !dev_h || dtype != c->p.dtype) return LEM_EINVAL;
+  c->h = dev_h;
+  if (!c->frozen) c->rec_valid = false;
+  c->lev_valid = c->frozen && c->lev_valid;
+  c->acc_valid = c->frozen && c->acc_valid;
+  return LEM_OK;
+}
+
+int lem_set_uplift_field(lem_ctx* c, const double* dev_U) {
+  if (!c) return LEM_EINVAL;
+  c->Uf = dev_U;
+  return LEM_OK;
+}
+
+int lem_receivers(lem_ctx* c, int32_t* dev_rec) {
+  if (!c) return LEM_EINVAL;
+  if (!c->h && !c->frozen) return LEM_ESTATE;
+  int rc = launch_step(c, kPhRec, 1);
+  if (rc != LEM_OK) return rc;
+  c->rec_valid = true;
+  c->lev_valid = c->acc_valid = false;
+  if (dev_rec) {
+    export_rec_kernel<<<aux_grid(c), 256, 0, c->stream>>>(c->code, dev_rec, c->N, c->p.nx);
+    LEM_CUDA(cudaGetLastError());
+  }
+  return LEM_OK;
+}
+
+int lem_donors(lem_ctx* c, int32_t* dev_dnum, int32_t* dev_donor) {
+  if (!c) return LEM_EINVAL;
+  if (!c->rec_valid) return LEM_ESTATE;
+  if (dev_dnum || dev_donor) {
+    export_donors_kernel<<<aux_grid(c), 256, 0, c->stream>>>(c->mask, dev_dnum, dev_donor, c->N,
+                                                             c->p.nx);
+    LEM_CUDA(cudaGetLastError());
+  }
+  return LEM_OK;
+}
+
+int lem_levels(lem_ctx* c, int64_t* nlevels, int32_t* dev_queue, int64_t* dev_levels,
+               int32_t* dev_depth) {
+  if (!c) return LEM_EINVAL;
+  if (!c->rec_valid) return LEM_ESTATE;
+  int rc = launch_step(c, kPhLev, 1);
+  if (rc != LEM_OK) return rc;
+  int L = 0;
+  rc = read_status(c, &L);
+  if (rc != LEM_OK) {
+    c->lev_valid = false;
+    return rc;
+  }
+  c->lev_valid = true;
+  c->acc_valid = false;
+  if (nlevels) *nlevels = L;
+  if (dev_queue)
+    LEM_CUDA(cudaMemcpyAsync(dev_queue, c->queue, (size_t)c->N * sizeof(int),
+                             cudaMemcpyDeviceToDevice, c->stream));
+  if (dev_levels) {
+    export_levels_kernel<<<1 + L / 256, 256, 0, c->stream>>>(c->levels, dev_levels, L + 1);
+    LEM_CUDA(cudaGetLastError());
+  }
+  if (dev_depth) {
+    export_depth_kernel<<<aux_grid(c), 256, 0, c->stream>>>(c->queue, c->levels, L, dev_depth,
+                                                            c->N);
+    LEM_CUDA(cudaGetLastError());
+  }
+  return LEM_OK;
+}
+
+int lem_accumulate(lem_ctx* c, void* dev_counts) {
+  if (!c) return LEM_EINVAL;
+  if (!c->lev_valid) return LEM_ESTATE;
+  int rc = launch_step(c, kPhAcc, 1);
+  if (rc != LEM_OK) return rc;
+  c->acc_valid = true;
+  if (dev_counts)
+    LEM_CUDA(cudaMemcpyAsync(dev_counts, c->cnt, (size_t)c->N * (c->p.count_bits / 8),
+                             cudaMemcpyDeviceToDevice, c->stream));
+  return LEM_OK;
+}
+
+int lem_erode(lem_ctx* c) {
+  if (!c) return LEM_EINVAL;
+  if (!c->h) return LEM_ESTATE;
+  if (!c->acc_valid) return LEM_ESTATE;
+  int rc = launch_step(c, kPhEro, 1);
+  if (rc != LEM_OK) return rc;
+  if (!c->frozen) c->rec_valid = c->lev_valid = c->acc_valid = false;
+  return LEM_OK;
+}
+
+int lem_step(lem_ctx* c, int nsteps) {
+  if (!c || nsteps < 0) return LEM_EINVAL;
+  if (!c->h) return LEM_ESTATE;
+  if (nsteps == 0) return LEM_OK;
+  int rc = launch_step(c, kPhAll, nsteps);
+  if (rc != LEM_OK) return rc;
+  if (c->frozen) {
+    c->rec_valid = c->lev_valid = c->acc_valid = true;
+  } else {
+    c->rec_valid = c->lev_valid = c->acc_valid = false;
+  }
+  return LEM_OK;
+}
+
+int lem_set_receivers(lem_ctx* c, const int32_t* dev_rec) {
+  if (!c) return LEM_EINVAL;
+  c->rec_valid = c->lev_valid = c->acc_valid = false;
+  if (!dev_rec) {
+    c->frozen = false;
+    return LEM_OK;
+  }
+  import_rec_kernel<<<aux_grid(c), 256, 0, c->stream>>>(dev_rec, c->code, c->N, c->p.nx, c->p.ny,
+                                                        c->st);
+  LEM_CUDA(cudaGetLastError());
+  int rc = read_status(c, nullptr);
+  if (rc != LEM_OK) {
+    c->frozen = false;
+    return rc;
+  }
+  c->frozen = true;
+  rc = launch_step(c, kPhRec, 1);  // donor masks and level 0 of the frozen graph
+  if (rc != LEM_OK) return rc;
+  c->rec_valid = true;
+  return LEM_OK;
+}
+
+int lem_sync(lem_ctx* c) {
+  if (!c) return LEM_EINVAL;
+  return read_status(c, nullptr);
+}
+
+int lem_set_wait_limit(lem_ctx* c, double seconds) {
+  if (!c || !(seconds > 0) || !is_finite(seconds)) return LEM_EINVAL;
+  c->wait_limit_s = seconds;
+  unsigned long long ns = (unsigned long long)(seconds * 1e9);
+  LEM_CUDA(cudaMemcpyAsync(&c->st->wait_limit_ns, &ns, sizeof(ns), cudaMemcpyHostToDevice,
+                           c->stream));
+  LEM_CUDA(cudaStreamSynchronize(c->stream));
+  return LEM_OK;
+}
+
+int lem_selftest_wait(lem_ctx* c) {
+  if (!c) return LEM_EINVAL;
+  selftest_wait_kernel<<<1, 32, 0, c->stream>>>(c->st);
+  LEM_CUDA(cudaGetLastError());
+  return read_status(c, nullptr);
+}
+
+}  // extern "C"

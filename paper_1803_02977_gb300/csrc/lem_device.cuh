@@ -1,0 +1,160 @@
+// lem_device.cuh -- device-side building blocks shared by the library's
+// kernels: neighbour geometry, the status word, a bounded grid barrier and a
+// block-wide scan.  sm_103a only.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lem {
+
+// Receiver code of a cell: 0..7 = neighbour k (0=NW 1=N 2=NE 3=W 4=E 5=SW
+// 6=S 7=SE, ascending address order), 8 = no receiver (perimeter or pit).
+constexpr int kSink = 8;
+
+// Erosion factors are tabulated for counts below this bound.
+constexpr int kTableN = 1 << 16;
+
+// Status codes written into the device status word (same values as lem.h).
+constexpr int kErrInval = -1;
+constexpr int kErrTimeout = -4;
+
+// Phase bits of the persistent step kernel.
+constexpr int kPhRec = 1;     // Alg 1 receivers + Alg 2 donor masks + level 0
+constexpr int kPhLev = 2;     // Alg 3 breadth-first levels
+constexpr int kPhAcc = 4;     // Alg 4 accumulation
+constexpr int kPhEro = 8;     // Alg 5 + Alg 6
+constexpr int kPhAll = 15;
+
+__host__ __device__ __forceinline__ int nbr_dx(int k) {
+  return (k == 0 || k == 3 || k == 5) ? -1 : ((k == 2 || k == 4 || k == 7) ? 1 : 0);
+}
+__host__ __device__ __forceinline__ int nbr_dy(int k) { return k < 3 ? -1 : (k < 5 ? 0 : 1); }
+__host__ __device__ __forceinline__ bool nbr_diag(int k) {
+  return k == 0 || k == 2 || k == 5 || k == 7;
+}
+__host__ __device__ __forceinline__ int nbr_off(int k, int nx) { return nbr_dy(k) * nx + nbr_dx(k); }
+
+// Double nearest 1/sqrt(2), the diagonal slope weight (dist = dx*sqrt(2)).
+constexpr double kInvSqrt2 = 0.70710678118654752440;
+// Double nearest sqrt(2).
+constexpr double kSqrt2 = 1.41421356237309504880;
+
+// Global state of one context: grid-barrier words, sticky status, and the
+// hand-off words of the single-block narrow-level mode.
+struct DevState {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int err;
+  int nlevels;
+  int bfs_lo, bfs_hi, bfs_level, bfs_done;
+  unsigned long long wait_limit_ns;
+  int selftest_flag;  // never written by anyone: the self-test waits on it
+  int pad[3];
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void set_error(DevState* st, int code) { atomicCAS(&st->err, 0, code); }
+
+// Device-wide barrier for a co-resident (cooperative) grid.  Thread 0 of each
+// block arrives on a counter; the last arrival resets it and advances the
+// generation word that the others wait on.  Every wait is bounded by the
+// context's wait limit and abandons early when another block has recorded an
+// error; either way the function returns false and the caller must return.
+__device__ __forceinline__ bool grid_barrier(DevState* st, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned gen = ld_acquire(&st->bar_gen);
+    __threadfence();
+    unsigned arrived = atomicAdd(&st->bar_count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&st->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&st->bar_gen, 1u);
+    } else {
+      unsigned long long t0 = global_ns();
+      unsigned it = 0;
+      while (ld_acquire(&st->bar_gen) == gen) {
+        if ((++it & 31u) == 0) {
+          if (ld_volatile(&st->err) != 0) {
+            ok = 0;
+            break;
+          }
+          if (global_ns() - t0 > st->wait_limit_ns) {
+            set_error(st, kErrTimeout);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Exclusive block-wide scan of one int per thread; *total receives the sum.
+// scratch must hold BD/32 ints of shared memory.  Contains __syncthreads.
+template <int BD>
+__device__ __forceinline__ int block_exclusive_scan(int v, int* total, int* scratch) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) scratch[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = (lane < BD / 32) ? scratch[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < BD / 32) scratch[lane] = s;
+  }
+  __syncthreads();
+  int prefix = (w > 0) ? scratch[w - 1] : 0;
+  *total = scratch[BD / 32 - 1];
+  __syncthreads();
+  return prefix + x - v;
+}
+
+template <int BD>
+__device__ __forceinline__ long long block_sum(long long v, long long* scratch) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  long long s = 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < BD / 32; ++i) s += scratch[i];
+    scratch[0] = s;
+  }
+  __syncthreads();
+  s = scratch[0];
+  __syncthreads();
+  return s;
+}
+
+}  // namespace lem

@@ -1,0 +1,244 @@
+"""ctypes binding of liblem.so (include/lem.h), one function per C entry point.
+
+Argument marshalling only: torch tensors supply device memory and the CUDA
+stream, every computation runs in the library's CUDA kernels.  There is no
+CPU fallback: if the compiled library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+LEM_OK, LEM_EINVAL, LEM_ENOMEM, LEM_ECUDA, LEM_ETIMEOUT, LEM_ESTATE, LEM_EOVERFLOW = \
+    0, -1, -2, -3, -4, -5, -6
+LEM_F64, LEM_F32 = 0, 1
+
+_lib = None
+
+
+class LemError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = lib().lem_status_string(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+class lem_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double),
+                ("K", ctypes.c_double), ("m", ctypes.c_double), ("U", ctypes.c_double),
+                ("dt", ctypes.c_double), ("area_scale", ctypes.c_double),
+                ("dtype", ctypes.c_int), ("count_bits", ctypes.c_int)]
+
+
+# (name, restype, argtypes) of every entry point declared in include/lem.h
+_VP, _I, _D, _I64P = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = [
+    ("lem_create", _I, [ctypes.POINTER(_VP), _I, _I, _D, _D, _D, _D, _D]),
+    ("lem_create_ex", _I, [ctypes.POINTER(_VP), ctypes.POINTER(lem_params)]),
+    ("lem_destroy", None, [_VP]),
+    ("lem_set_stream", _I, [_VP, _VP]),
+    ("lem_bind_elevation", _I, [_VP, _VP, _I]),
+    ("lem_set_uplift_field", _I, [_VP, _VP]),
+    ("lem_receivers", _I, [_VP, _VP]),
+    ("lem_donors", _I, [_VP, _VP, _VP]),
+    ("lem_levels", _I, [_VP, _I64P, _VP, _VP, _VP]),
+    ("lem_accumulate", _I, [_VP, _VP]),
+    ("lem_erode", _I, [_VP]),
+    ("lem_step", _I, [_VP, _I]),
+    ("lem_set_receivers", _I, [_VP, _VP]),
+    ("lem_sync", _I, [_VP]),
+    ("lem_set_wait_limit", _I, [_VP, _D]),
+    ("lem_selftest_wait", _I, [_VP]),
+    ("lem_status_string", ctypes.c_char_p, [_I]),
+]
+
+
+def lib(build_if_missing: bool = True):
+    """Load liblem.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB_PATH
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"liblem.so is not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, where):
+    if status != LEM_OK:
+        raise LemError(status, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---- one Python function per C entry point --------------------------------
+
+def lem_create(nx, ny, dx, K, m, U, dt):
+    h = _VP()
+    _check(lib().lem_create(ctypes.byref(h), nx, ny, dx, K, m, U, dt), "lem_create")
+    return h
+
+
+def lem_create_ex(nx, ny, dx, K, m, U, dt, area_scale=0.0, dtype=LEM_F64, count_bits=32):
+    p = lem_params(nx, ny, dx, K, m, U, dt, area_scale, dtype, count_bits)
+    h = _VP()
+    _check(lib().lem_create_ex(ctypes.byref(h), ctypes.byref(p)), "lem_create_ex")
+    return h
+
+
+def lem_destroy(ctx):
+    lib().lem_destroy(ctx)
+
+
+def lem_set_stream(ctx, stream=None):
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(lib().lem_set_stream(ctx, ctypes.c_void_p(s)), "lem_set_stream")
+
+
+def lem_bind_elevation(ctx, h, dtype):
+    _check(lib().lem_bind_elevation(ctx, _ptr(h), dtype), "lem_bind_elevation")
+
+
+def lem_set_uplift_field(ctx, U):
+    _check(lib().lem_set_uplift_field(ctx, _ptr(U)), "lem_set_uplift_field")
+
+
+def lem_receivers(ctx, rec=None):
+    _check(lib().lem_receivers(ctx, _ptr(rec)), "lem_receivers")
+
+
+def lem_donors(ctx, dnum=None, donor=None):
+    _check(lib().lem_donors(ctx, _ptr(dnum), _ptr(donor)), "lem_donors")
+
+
+def lem_levels(ctx, queue=None, levels=None, depth=None):
+    L = ctypes.c_int64(0)
+    _check(lib().lem_levels(ctx, ctypes.byref(L), _ptr(queue), _ptr(levels), _ptr(depth)),
+           "lem_levels")
+    return L.value
+
+
+def lem_accumulate(ctx, counts=None):
+    _check(lib().lem_accumulate(ctx, _ptr(counts)), "lem_accumulate")
+
+
+def lem_erode(ctx):
+    _check(lib().lem_erode(ctx), "lem_erode")
+
+
+def lem_step(ctx, nsteps):
+    _check(lib().lem_step(ctx, nsteps), "lem_step")
+
+
+def lem_set_receivers(ctx, rec):
+    _check(lib().lem_set_receivers(ctx, _ptr(rec)), "lem_set_receivers")
+
+
+def lem_sync(ctx):
+    _check(lib().lem_sync(ctx), "lem_sync")
+
+
+def lem_set_wait_limit(ctx, seconds):
+    _check(lib().lem_set_wait_limit(ctx, seconds), "lem_set_wait_limit")
+
+
+def lem_selftest_wait(ctx):
+    """Returns the raw status (LEM_ETIMEOUT expected)."""
+    return lib().lem_selftest_wait(ctx)
+
+
+# ---- convenience wrapper ------------------------------------------------------
+
+class Model:
+    """One grid: a context plus the bound elevation tensor (ny, nx) on cuda."""
+
+    def __init__(self, h, dx=100.0, K=1e-5, m=0.5, U=1e-3, dt=1000.0, area_scale=0.0,
+                 count_bits=32, stream=None):
+        if h.dtype == torch.float64:
+            self.dtype = LEM_F64
+        elif h.dtype == torch.float32:
+            self.dtype = LEM_F32
+        else:
+            raise ValueError("elevations must be float64 or float32")
+        self.h = h.contiguous()
+        self.ny, self.nx = self.h.shape
+        self.count_bits = count_bits
+        self.ctx = lem_create_ex(self.nx, self.ny, dx, K, m, U, dt, area_scale, self.dtype,
+                                 count_bits)
+        lem_set_stream(self.ctx, stream)
+        lem_bind_elevation(self.ctx, self.h, self.dtype)
+        self._Uf = None
+
+    @property
+    def N(self):
+        return self.nx * self.ny
+
+    def close(self):
+        if self.ctx:
+            lem_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_uplift_field(self, Uf):
+        self._Uf = None if Uf is None else Uf.to(torch.float64).contiguous()
+        lem_set_uplift_field(self.ctx, self._Uf)
+
+    def receivers(self):
+        rec = torch.empty(self.N, dtype=torch.int32, device=self.h.device)
+        lem_receivers(self.ctx, rec)
+        return rec
+
+    def donors(self):
+        dnum = torch.empty(self.N, dtype=torch.int32, device=self.h.device)
+        donor = torch.empty(self.N * 8, dtype=torch.int32, device=self.h.device)
+        lem_donors(self.ctx, dnum, donor)
+        return dnum, donor.view(self.N, 8)
+
+    def levels(self, want_depth=True):
+        q = torch.empty(self.N, dtype=torch.int32, device=self.h.device)
+        lev = torch.empty(self.N + 1, dtype=torch.int64, device=self.h.device)
+        depth = torch.empty(self.N, dtype=torch.int32, device=self.h.device) if want_depth else None
+        L = lem_levels(self.ctx, q, lev, depth)
+        return q, lev[:L + 1], depth
+
+    def accumulate(self):
+        dt = torch.int64 if self.count_bits == 64 else torch.int32
+        cnt = torch.empty(self.N, dtype=dt, device=self.h.device)
+        lem_accumulate(self.ctx, cnt)
+        return cnt
+
+    def erode(self):
+        lem_erode(self.ctx)
+
+    def step(self, nsteps=1):
+        lem_step(self.ctx, nsteps)
+
+    def set_receivers(self, rec):
+        lem_set_receivers(self.ctx, rec)
+
+    def sync(self):
+        lem_sync(self.ctx)

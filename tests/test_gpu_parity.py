@@ -1,0 +1,238 @@
+"""Stage-by-stage parity of the CUDA path (through the C ABI) against the
+oracle on identical inputs: integer stages bit for bit, FP64 elevations within
+1e-12 relative per step, FP32 elevations within the FP32 bound."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_02977_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL64 = 1e-12
+
+
+def _lem():
+    from paper_1803_02977_gb300 import lem
+    return lem
+
+
+def _dev():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return torch.device("cuda:0")
+
+
+def _int_grid(nx, ny, seed, levels=5):
+    u = synth.uniform01(seed, nx * ny).reshape(ny, nx)
+    return np.floor(u * levels)
+
+
+def _tilted(nx, ny, seed, slope=0.05):
+    # a plane falling toward the west edge plus small noise: long flow paths,
+    # many levels (exercises the narrow single-block mode and the wide mode)
+    x = np.arange(nx, dtype=np.float64)[None, :]
+    h = slope * 100.0 * x + 0.01 * synth.uniform01(seed, nx * ny).reshape(ny, nx)
+    h[0, :] = h[-1, :] = h[:, 0] = h[:, -1] = 0.0
+    return h
+
+
+CASES = [
+    ("3x3", lambda: synth.noise_surface(3, 3, 1)),
+    ("5x4", lambda: synth.noise_surface(5, 4, 2)),
+    ("17x13", lambda: synth.noise_surface(17, 13, 3)),
+    ("64x64_int", lambda: _int_grid(64, 64, 4)),
+    ("flat_40x30", lambda: np.zeros((30, 40))),
+    ("plateau_50x50", lambda: np.pad(np.full((48, 48), 7.0), 1)),
+    ("256x256", lambda: synth.noise_surface(256, 256, 1)),
+    ("333x517", lambda: synth.noise_surface(333, 517, 5)),
+    ("tilted_300x200", lambda: _tilted(300, 200, 6)),
+    ("tilted_1500x64", lambda: _tilted(1500, 64, 7, slope=0.2)),
+    ("1031x777_int", lambda: _int_grid(1031, 777, 8, levels=40)),
+]
+
+
+def _run_stages(h_np, dtype=torch.float64, count_bits=32, **par):
+    lem = _lem()
+    dev = _dev()
+    h = torch.tensor(h_np, dtype=dtype, device=dev).contiguous()
+    mdl = lem.Model(h, count_bits=count_bits, **par)
+    rec = mdl.receivers()
+    dnum, donor = mdl.donors()
+    q, lev, depth = mdl.levels()
+    cnt = mdl.accumulate()
+    mdl.erode()
+    mdl.sync()
+    out = dict(rec=rec.cpu().numpy(), dnum=dnum.cpu().numpy(), donor=donor.cpu().numpy(),
+               queue=q.cpu().numpy(), levels=lev.cpu().numpy(), depth=depth.cpu().numpy(),
+               cnt=cnt.cpu().numpy(), h=h.cpu().numpy())
+    mdl.close()
+    return out
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_stages_fp64_bit_exact_and_tolerance(name, make):
+    h0 = make()
+    par = dict(dx=100.0, K=1e-4, m=0.5, U=1e-3, dt=1000.0)
+    g = _run_stages(h0, **par)
+    ref = oracle.StepGraph(h0)
+    assert np.array_equal(g["rec"], ref.rec)
+    assert np.array_equal(g["dnum"], ref.dnum)
+    assert np.array_equal(g["donor"], ref.donor)
+    assert np.array_equal(g["queue"], ref.queue)
+    assert np.array_equal(g["levels"], ref.levels)
+    assert np.array_equal(g["depth"], ref.depth)
+    assert np.array_equal(g["cnt"], ref.cnt)
+    p = oracle.params(**par)
+    want, _ = oracle.step(h0, p)
+    scale = max(np.abs(want).max(), 1.0)
+    assert np.abs(g["h"] - want).max() <= REL64 * scale
+
+
+def test_stages_int64_counts():
+    h0 = synth.noise_surface(300, 211, 9)
+    g = _run_stages(h0, count_bits=64)
+    ref = oracle.StepGraph(h0)
+    assert g["cnt"].dtype == np.int64
+    assert np.array_equal(g["cnt"], ref.cnt)
+
+
+@pytest.mark.parametrize("nx,ny,seed", [(256, 256, 1), (401, 173, 2), (64, 700, 3)])
+def test_fp32_integer_stages_bit_exact_and_erosion_bound(nx, ny, seed):
+    h32 = synth.noise_surface(nx, ny, seed).astype(np.float32)
+    par = dict(dx=100.0, K=2e-5, m=0.45, U=1e-3, dt=500.0)
+    g = _run_stages(h32, dtype=torch.float32, **par)
+    ref = oracle.StepGraph(h32)  # receivers on the promoted FP32 values
+    for key in ("rec", "dnum", "donor", "queue", "levels", "depth", "cnt"):
+        assert np.array_equal(g[key], getattr(ref, key)), key
+    want, _ = oracle.step(h32.astype(np.float64), oracle.params(**par))
+    # FP32 increment form: a few units of FP32 rounding of the elevation
+    tol = 4 * 2.0 ** -24 * np.maximum(np.abs(want), 1.0)
+    assert np.all(np.abs(g["h"].astype(np.float64) - want) <= tol)
+
+
+def test_step_matches_oracle_per_step():
+    lem = _lem()
+    dev = _dev()
+    w = synth.workload("grid256_f64")
+    p = oracle.params(dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt)
+    h_np = w.initial()
+    h = torch.tensor(h_np, device=dev)
+    mdl = lem.Model(h, dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt)
+    for _ in range(10):
+        before = h.cpu().numpy()
+        mdl.step(1)
+        mdl.sync()
+        want, _ = oracle.step(before, p)
+        got = h.cpu().numpy()
+        assert np.abs(got - want).max() <= REL64 * max(np.abs(want).max(), 1.0)
+    # several steps in one launch equal the same steps launched one by one
+    h2 = torch.tensor(h_np, device=dev)
+    m2 = lem.Model(h2, dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt)
+    m2.step(10)
+    m2.sync()
+    assert torch.equal(h, h2)
+    mdl.close()
+    m2.close()
+
+
+def test_uplift_field():
+    lem = _lem()
+    dev = _dev()
+    nx, ny = 120, 90
+    h0 = synth.noise_surface(nx, ny, 21)
+    Uf = 1e-3 * (1.0 + 0.5 * synth.signed_field(nx, ny, 22))
+    par = dict(dx=100.0, K=3e-5, m=0.5, U=0.0, dt=1000.0)
+    h = torch.tensor(h0, device=dev)
+    mdl = lem.Model(h, **par)
+    mdl.set_uplift_field(torch.tensor(Uf, device=dev))
+    mdl.step(1)
+    mdl.sync()
+    want, _ = oracle.step(h0, oracle.params(**dict(par, Ufield=Uf)))
+    assert np.abs(h.cpu().numpy() - want).max() <= REL64 * np.abs(want).max()
+
+
+def test_frozen_channel_closed_form():
+    lem = _lem()
+    dev = _dev()
+    nx = 200
+    dx, K, m, U, dt = 100.0, 1e-5, 0.5, 1e-3, 1000.0
+    rec = np.arange(3 * nx, dtype=np.int32)
+    for x in range(1, nx - 1):
+        rec[nx + x] = nx + x - 1
+    area = dx * dx
+    prof = np.zeros((3, nx))
+    for x in range(1, nx - 1):
+        prof[1, x] = prof[1, x - 1] + dx * U / (K * ((nx - 1 - x) * area) ** m)
+    h = torch.tensor(prof, device=dev)
+    mdl = lem.Model(h, dx=dx, K=K, m=m, U=U, dt=dt)
+    mdl.set_receivers(torch.tensor(rec, device=dev))
+    mdl.step(3)
+    mdl.sync()
+    assert np.abs(h.cpu().numpy() - prof).max() <= 1e-12 * prof.max()
+    q, lev, depth = mdl.levels()
+    assert lev.numel() == nx  # level 0 plus one level per chain cell: L = nx-1
+    mdl.close()
+
+
+def test_frozen_cycle_is_reported():
+    lem = _lem()
+    dev = _dev()
+    nx, ny = 6, 5
+    rec = np.arange(nx * ny, dtype=np.int32)
+    a, b = 2 * nx + 2, 2 * nx + 3
+    rec[a], rec[b] = b, a  # two interior cells draining into each other
+    h = torch.zeros((ny, nx), dtype=torch.float64, device=dev)
+    mdl = lem.Model(h)
+    mdl.set_receivers(torch.tensor(rec, device=dev))
+    with pytest.raises(lem.LemError) as e:
+        mdl.levels()
+    assert e.value.status == lem.LEM_EINVAL
+    bad = np.arange(nx * ny, dtype=np.int32)
+    bad[2 * nx + 2] = 0  # not a neighbour
+    with pytest.raises(lem.LemError) as e:
+        mdl.set_receivers(torch.tensor(bad, device=dev))
+    assert e.value.status == lem.LEM_EINVAL
+    mdl.close()
+
+
+def test_state_errors_and_timeout_path():
+    lem = _lem()
+    dev = _dev()
+    h = torch.tensor(synth.noise_surface(32, 32, 3), device=dev)
+    mdl = lem.Model(h)
+    with pytest.raises(lem.LemError) as e:
+        mdl.levels()
+    assert e.value.status == lem.LEM_ESTATE
+    with pytest.raises(lem.LemError) as e:
+        mdl.erode()
+    assert e.value.status == lem.LEM_ESTATE
+    lem.lem_set_wait_limit(mdl.ctx, 0.02)
+    assert lem.lem_selftest_wait(mdl.ctx) == lem.LEM_ETIMEOUT
+    lem.lem_set_wait_limit(mdl.ctx, 2.0)
+    # the context stays usable after the timed-out wait
+    before = h.cpu().numpy()
+    mdl.step(1)
+    mdl.sync()
+    want, _ = oracle.step(before, oracle.params())
+    assert np.abs(h.cpu().numpy() - want).max() <= REL64 * np.abs(want).max()
+    mdl.close()
+
+
+def test_determinism_repeat():
+    lem = _lem()
+    dev = _dev()
+    h_np = synth.noise_surface(700, 500, 44)
+    outs = []
+    for _ in range(2):
+        h = torch.tensor(h_np, device=dev)
+        mdl = lem.Model(h)
+        mdl.receivers()
+        q, lev, _ = mdl.levels(want_depth=False)
+        cnt = mdl.accumulate()
+        mdl.erode()
+        mdl.sync()
+        outs.append((q.cpu(), lev.cpu(), cnt.cpu(), h.cpu()))
+        mdl.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
