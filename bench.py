@@ -267,6 +267,9 @@ def run_ours(args):
     value = N * K * ws / (tot_ms / 1e3)
     ms_per_step = tot_ms / K
 
+    # one traced step after the timed region: in-kernel time per phase
+    timeline = traced_step(lem, mdl, flush)
+
     # level count of the state reached (outside the timed region)
     mdl.receivers()
     L = lem.lem_levels(mdl.ctx)
@@ -351,7 +354,7 @@ def run_ours(args):
             "config": config_of(w, args), "levels_after": int(L),
             "step_ms_min_median_max": [min(step_ms), float(np.median(step_ms)), max(step_ms)],
             "wall_s_timed_region": t_wall,
-            "roofline": roofline, "phases": phases, "clocks": clk,
+            "roofline": roofline, "phases": phases, "timeline": timeline, "clocks": clk,
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": N * P,
                     "d2h_bytes_per_step": N * P, "steps": Ke},
             "gpu_launches": K, "cpu_baseline": cpu}
@@ -361,6 +364,36 @@ def run_ours(args):
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def traced_step(lem, mdl, flush):
+    """One step with device-side tracing: microseconds spent in each phase
+    (segments between consecutive device-wide barriers, as seen by block 0)."""
+    lem.lem_trace_enable(mdl.ctx, 1 << 16)
+    flush.zero_()
+    mdl.step(2)  # the first step ends at a device-wide barrier: all blocks done
+    tr = lem.lem_trace_read(mdl.ctx, 1 << 16)
+    lem.lem_trace_enable(mdl.ctx, 0)
+    ends = [i for i, e in enumerate(tr) if e[1] == "step_end"]
+    if ends:
+        tr = tr[:ends[0] + 1]
+    if len(tr) < 2:
+        return None
+    group = {"receivers": "receivers", "level0": "receivers", "bfs_wide": "levels",
+             "bfs_narrow": "levels", "acc_wide": "accumulate", "acc_narrow": "accumulate",
+             "uplift": "erode", "erode_wide": "erode", "erode_narrow": "erode",
+             "private_levels": "levels", "private_accumulate": "accumulate",
+             "private_erode": "erode", "step_end": "erode"}
+    out = {"receivers": 0.0, "levels": 0.0, "accumulate": 0.0, "erode": 0.0}
+    barriers = {"wide_levels": 0, "narrow_runs": 0}
+    for (t0, _, _), (t1, ph, _) in zip(tr[:-1], tr[1:]):
+        out[group.get(ph, "receivers")] += (t1 - t0) / 1e3
+        if ph.endswith("_wide"):
+            barriers["wide_levels"] += 1
+        elif ph.endswith("_narrow"):
+            barriers["narrow_runs"] += 1
+    return {"us": out, "total_us": (tr[-1][0] - tr[0][0]) / 1e3, "segments": len(tr) - 1,
+            **barriers}
 
 
 def measured_peaks():

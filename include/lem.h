@@ -172,6 +172,34 @@ LEM_API int lem_set_wait_limit(lem_ctx* ctx, double seconds);
  * the context stays usable.  Exercises the timeout path without a fault. */
 LEM_API int lem_selftest_wait(lem_ctx* ctx);
 
+/* How lem_step runs Algs 3-6.  Mode 0 (default): each thread block expands,
+ * accumulates and erodes the trees grown from its own share of the cells
+ * without receiver in a private queue, so levels need only block-level
+ * barriers (the paper's private queues, Section "Independent Parallelism");
+ * if any block's forest exceeds twice its fair share of cells the step is
+ * redone on device-wide levels.  Mode 1: device-wide levels only, one grid
+ * barrier per level (the paper's level-synchronous queue).  Both give the
+ * same elevations; the integer stages are identical. */
+LEM_API int lem_set_step_mode(lem_ctx* ctx, int mode);
+
+/* Number of lem_step steps completed on block-private queues and on
+ * device-wide levels since the context was created (synchronises). */
+LEM_API int lem_step_stats(lem_ctx* ctx, int64_t* private_steps, int64_t* device_wide_steps);
+
+/* Device-side tracing of the step kernel's timeline: with capacity > 0,
+ * later launches record, after every device-wide barrier, the GPU global
+ * timer (ns) and a tag (phase << 16 | level); capacity 0 turns tracing off.
+ * Tracing costs one store per barrier. */
+LEM_API int lem_trace_enable(lem_ctx* ctx, int capacity);
+
+/* Copy up to `cap` recorded entries to host arrays ns[] and tags[] and clear
+ * the record (synchronises the stream).  *n receives the number of entries
+ * recorded since the last read (entries beyond the capacity are dropped).
+ * Tags: 1 start, 2 receivers, 3 level 0, 4 wide level, 5 narrow levels,
+ * 6 wide accumulation, 7 narrow accumulation, 8 uplift, 9 wide erosion,
+ * 10 narrow erosion. */
+LEM_API int lem_trace_read(lem_ctx* ctx, int64_t* ns, int32_t* tags, int cap, int* n);
+
 /* Static description of a status code. */
 LEM_API const char* lem_status_string(int status);
 

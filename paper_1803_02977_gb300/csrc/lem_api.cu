@@ -4,9 +4,11 @@
 // the paper's exported layouts (Table 1: Rec, Donor/Dnum, Queue, Levels,
 // Accum).
 #include <cmath>
+#include <cstddef>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "lem.h"
 #include "lem_step_kernel.cuh"
@@ -25,15 +27,19 @@ struct lem_ctx {
   int* queue = nullptr;
   int* levels = nullptr;
   void* cnt = nullptr;
-  double* Ftab = nullptr;
+  double2* Ftab = nullptr;
   float* gtab = nullptr;
   DevState* st = nullptr;
   int* partial = nullptr;
+  int* pq = nullptr;  // block-private queues, pcap entries per block
+  int pcap = 0;
+  int mode = 0;       // 0: block-private levels with fallback, 1: device-wide only
   int grid = 0;
   int* host_status = nullptr;  // pinned: [err, nlevels]
   bool rec_valid = false, lev_valid = false, acc_valid = false, frozen = false;
   double Kdt = 0, dxd = 0, area_scale = 0;
   double wait_limit_s = 2.0;
+  unsigned long long* trace = nullptr;  // device trace buffer (lem_trace_enable)
 };
 
 namespace {
@@ -50,15 +56,18 @@ int cuda_status(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_status(e_); \
   } while (0)
 
-__global__ void build_tables_kernel(double* Ftab, float* gtab, double Kdt, double m, double dx,
+// Erosion factors by cell count: F = K*dt*(count*area_scale)^m / d with the
+// same operation order as the per-cell expression, its correctly rounded
+// reciprocal 1/(1+F), and g = F/(1+F) rounded once to float.
+__global__ void build_tables_kernel(double2* Ftab, float* gtab, double Kdt, double m, double dx,
                                     double dxd, double area_scale) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kTableN; i += gridDim.x * blockDim.x) {
     const double A = __dmul_rn((double)i, area_scale);
     const double P = __dmul_rn(Kdt, pow(A, m));
     const double Fc = __ddiv_rn(P, dx);
     const double Fd = __ddiv_rn(P, dxd);
-    Ftab[i] = Fc;
-    Ftab[kTableN + i] = Fd;
+    Ftab[i] = make_double2(Fc, __drcp_rn(__dadd_rn(1.0, Fc)));
+    Ftab[kTableN + i] = make_double2(Fd, __drcp_rn(__dadd_rn(1.0, Fd)));
     gtab[i] = (float)(Fc / (1.0 + Fc));
     gtab[kTableN + i] = (float)(Fd / (1.0 + Fd));
   }
@@ -68,7 +77,7 @@ __global__ void export_rec_kernel(const uint8_t* __restrict__ code, int32_t* __r
                                   int N, int nx) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
     const int k = code[c];
-    rec[c] = (k == kSink) ? c : c + nbr_off(k, nx);
+    rec[c] = no_receiver(k) ? c : c + nbr_off(k, nx);
   }
 }
 
@@ -114,7 +123,7 @@ __global__ void import_rec_kernel(const int32_t* __restrict__ rec, uint8_t* __re
     const int r = rec[c];
     const int x = c % nx, y = c / nx;
     const bool perim = (x == 0 || y == 0 || x == nx - 1 || y == ny - 1);
-    int k = kSink;
+    int k = perim ? kEdge : kSink;
     if (r != c) {
       if (perim || r < 0 || r >= N) {
         set_error(st, kErrInval);
@@ -122,7 +131,7 @@ __global__ void import_rec_kernel(const int32_t* __restrict__ rec, uint8_t* __re
         const int ddx = r % nx - x, ddy = r / nx - y;
         for (int q = 0; q < 8; ++q)
           if (nbr_dx(q) == ddx && nbr_dy(q) == ddy) k = q;
-        if (k == kSink) set_error(st, kErrInval);
+        if (k >= kSink) set_error(st, kErrInval);
       }
     }
     code[c] = (uint8_t)k;
@@ -176,6 +185,8 @@ StepArgs<HT, CT> make_args(lem_ctx* c, int phases, int nsteps) {
   a.gtab = c->gtab;
   a.st = c->st;
   a.partial = c->partial;
+  a.pq = c->pq;
+  a.pcap = c->pcap;
   a.phases = phases;
   a.nsteps = nsteps;
   a.frozen = c->frozen ? 1 : 0;
@@ -287,16 +298,20 @@ int lem_create_ex(lem_ctx** out, const lem_params* pin) {
   if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
   if (e == cudaSuccess) {
     c->grid = nsm * (per_sm < 2 ? per_sm : 2);
+    // private queue share: twice the fair share of cells, at least 4096
+    const long long fair = ((long long)c->N + c->grid - 1) / c->grid;
+    c->pcap = (int)(2 * fair > 4096 ? 2 * fair : 4096);
     e = cudaMalloc(&c->code, N);
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->mask, N);
   if (e == cudaSuccess) e = cudaMalloc(&c->queue, N * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->levels, (N + 2) * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->cnt, N * (p.count_bits / 8));
-  if (e == cudaSuccess) e = cudaMalloc(&c->Ftab, 2 * kTableN * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->Ftab, 2 * kTableN * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc(&c->gtab, 2 * kTableN * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&c->st, sizeof(DevState));
   if (e == cudaSuccess) e = cudaMalloc(&c->partial, (size_t)c->grid * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->pq, (size_t)c->grid * c->pcap * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&c->host_status, 4 * sizeof(int));
   if (e == cudaSuccess) {
     DevState s;
@@ -329,6 +344,8 @@ void lem_destroy(lem_ctx* c) {
   cudaFree(c->gtab);
   cudaFree(c->st);
   cudaFree(c->partial);
+  cudaFree(c->pq);
+  cudaFree(c->trace);
   if (c->host_status) cudaFreeHost(c->host_status);
   delete c;
 }
@@ -435,7 +452,7 @@ int lem_step(lem_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return LEM_EINVAL;
   if (!c->h) return LEM_ESTATE;
   if (nsteps == 0) return LEM_OK;
-  int rc = launch_step(c, kPhAll, nsteps);
+  int rc = launch_step(c, c->mode == 0 ? (kPhRec | kPhPrivate) : kPhAll, nsteps);
   if (rc != LEM_OK) return rc;
   if (c->frozen) {
     c->rec_valid = c->lev_valid = c->acc_valid = true;
@@ -479,6 +496,67 @@ int lem_set_wait_limit(lem_ctx* c, double seconds) {
   LEM_CUDA(cudaMemcpyAsync(&c->st->wait_limit_ns, &ns, sizeof(ns), cudaMemcpyHostToDevice,
                            c->stream));
   LEM_CUDA(cudaStreamSynchronize(c->stream));
+  return LEM_OK;
+}
+
+int lem_set_step_mode(lem_ctx* c, int mode) {
+  if (!c || (mode != 0 && mode != 1)) return LEM_EINVAL;
+  c->mode = mode;
+  return LEM_OK;
+}
+
+int lem_step_stats(lem_ctx* c, int64_t* private_steps, int64_t* device_wide_steps) {
+  if (!c) return LEM_EINVAL;
+  LEM_CUDA(cudaStreamSynchronize(c->stream));
+  int v[2] = {0, 0};
+  LEM_CUDA(cudaMemcpy(&v[0], (char*)c->st + offsetof(DevState, private_steps), sizeof(int),
+                      cudaMemcpyDeviceToHost));
+  LEM_CUDA(cudaMemcpy(&v[1], (char*)c->st + offsetof(DevState, global_steps), sizeof(int),
+                      cudaMemcpyDeviceToHost));
+  if (private_steps) *private_steps = v[0];
+  if (device_wide_steps) *device_wide_steps = v[1];
+  return LEM_OK;
+}
+
+int lem_trace_enable(lem_ctx* c, int capacity) {
+  if (!c || capacity < 0) return LEM_EINVAL;
+  LEM_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->trace) {
+    cudaFree(c->trace);
+    c->trace = nullptr;
+  }
+  if (capacity > 0) LEM_CUDA(cudaMalloc(&c->trace, 2 * sizeof(unsigned long long) * capacity));
+  const int capn[2] = {capacity, 0};  // trace_cap, trace_n (adjacent)
+  LEM_CUDA(cudaMemcpy((char*)c->st + offsetof(DevState, trace), &c->trace, sizeof(c->trace),
+                      cudaMemcpyHostToDevice));
+  LEM_CUDA(cudaMemcpy((char*)c->st + offsetof(DevState, trace_cap), capn, sizeof(capn),
+                      cudaMemcpyHostToDevice));
+  return LEM_OK;
+}
+
+int lem_trace_read(lem_ctx* c, int64_t* ns, int32_t* tags, int cap, int* n) {
+  if (!c || cap < 0 || (cap > 0 && (!ns || !tags))) return LEM_EINVAL;
+  LEM_CUDA(cudaStreamSynchronize(c->stream));
+  int cnt = 0, tcap = 0;
+  LEM_CUDA(cudaMemcpy(&tcap, (char*)c->st + offsetof(DevState, trace_cap), sizeof(int),
+                      cudaMemcpyDeviceToHost));
+  LEM_CUDA(cudaMemcpy(&cnt, (char*)c->st + offsetof(DevState, trace_n), sizeof(int),
+                      cudaMemcpyDeviceToHost));
+  if (n) *n = cnt;
+  int m = cnt < cap ? cnt : cap;
+  if (m > tcap) m = tcap;
+  if (m > 0) {
+    std::vector<unsigned long long> buf(2 * (size_t)m);
+    LEM_CUDA(cudaMemcpy(buf.data(), c->trace, buf.size() * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost));
+    for (int i = 0; i < m; ++i) {
+      ns[i] = (int64_t)buf[2 * i];
+      tags[i] = (int32_t)buf[2 * i + 1];
+    }
+  }
+  const int zero = 0;
+  LEM_CUDA(cudaMemcpy((char*)c->st + offsetof(DevState, trace_n), &zero, sizeof(int),
+                      cudaMemcpyHostToDevice));
   return LEM_OK;
 }
 

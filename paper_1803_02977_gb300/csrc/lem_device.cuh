@@ -9,8 +9,11 @@
 namespace lem {
 
 // Receiver code of a cell: 0..7 = neighbour k (0=NW 1=N 2=NE 3=W 4=E 5=SW
-// 6=S 7=SE, ascending address order), 8 = no receiver (perimeter or pit).
+// 6=S 7=SE, ascending address order); 8 = interior cell without receiver
+// (a pit: uplifted, not eroded); 9 = perimeter cell (fixed base level).
 constexpr int kSink = 8;
+constexpr int kEdge = 9;
+__host__ __device__ __forceinline__ bool no_receiver(int code) { return code >= kSink; }
 
 // Erosion factors are tabulated for counts below this bound.
 constexpr int kTableN = 1 << 16;
@@ -25,6 +28,10 @@ constexpr int kPhLev = 2;     // Alg 3 breadth-first levels
 constexpr int kPhAcc = 4;     // Alg 4 accumulation
 constexpr int kPhEro = 8;     // Alg 5 + Alg 6
 constexpr int kPhAll = 15;
+// Algs 3-6 on block-private queues (each block expands, accumulates and
+// erodes the trees grown from its own cells without receiver), falling back
+// to the device-wide levels when a block's forest outgrows its share.
+constexpr int kPhPrivate = 16;
 
 __host__ __device__ __forceinline__ int nbr_dx(int k) {
   return (k == 0 || k == 3 || k == 5) ? -1 : ((k == 2 || k == 4 || k == 7) ? 1 : 0);
@@ -50,8 +57,45 @@ struct DevState {
   int bfs_lo, bfs_hi, bfs_level, bfs_done;
   unsigned long long wait_limit_ns;
   int selftest_flag;  // never written by anyone: the self-test waits on it
-  int pad[3];
+  int trace_cap;      // capacity of trace (entries); 0 = tracing off
+  int trace_n;        // entries written since the last read
+  int private_overflow;  // a block's private forest exceeded its capacity
+  unsigned long long* trace;  // pairs {globaltimer ns, tag}
+  int private_steps;     // steps completed on block-private queues
+  int global_steps;      // steps that fell back to device-wide levels
 };
+
+// Trace tags: phase in the high half, level (or 0) in the low half.
+enum TraceTag : int {
+  kTrStart = 1 << 16,     // kernel entered, step begins
+  kTrCodes = 2 << 16,     // receiver codes done (barrier passed)
+  kTrLevel0 = 3 << 16,    // donor masks and level 0 done
+  kTrBfsWide = 4 << 16,   // one wide breadth-first level done
+  kTrBfsNarrow = 5 << 16, // a run of narrow levels done by block 0
+  kTrAccWide = 6 << 16,
+  kTrAccNarrow = 7 << 16,
+  kTrUplift = 8 << 16,
+  kTrEroWide = 9 << 16,
+  kTrEroNarrow = 10 << 16,
+  kTrPrivBfs = 11 << 16,    // all blocks' private queues built (barrier passed)
+  kTrPrivAcc = 12 << 16,    // block 0 finished its private accumulation
+  kTrPrivEro = 13 << 16,    // block 0 finished its private erosion
+  kTrStepEnd = 14 << 16,    // end-of-step barrier passed
+};
+
+// Record a timestamp (block 0, thread 0 only; no-op when tracing is off).
+__device__ __forceinline__ void trace_point(DevState* st, int tag) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && st->trace_cap > 0) {
+    const int i = st->trace_n;
+    if (i < st->trace_cap) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      st->trace[2 * i] = t;
+      st->trace[2 * i + 1] = (unsigned long long)(unsigned)tag;
+    }
+    st->trace_n = i + 1;
+  }
+}
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;

@@ -3,19 +3,41 @@
 // Algorithms 1-6, on one GB300.
 //
 // One launch covers any subset of the stages (phase bits) for nsteps steps.
-// Stages are separated by device-wide barriers (grid_barrier); breadth-first
-// levels are processed one barrier apart ("for-parallel" loops of the
-// paper), except that a run of narrow levels (at most kNarrow cells each) is
-// processed by block 0 alone with block-local barriers while the other blocks
-// wait once (the paper's barrier elimination, Section "On Parallelism").
+//
+// Receivers and donor masks (Algs 1-2) are grid-wide stencils; each block
+// owns a contiguous chunk of cells and each warp a contiguous sub-chunk, so
+// the cells without receiver (level 0 of Alg 3) are compacted in ascending
+// address order with warp ballots and one block-level prefix.
+//
+// Algs 3-6 then run in one of two forms:
+//  * block-private (lem_step): block b expands the breadth-first levels of
+//    the trees rooted at its own level-0 cells into a private queue, then
+//    accumulates (Alg 4) and erodes (Algs 5-6) exactly those trees.  Every
+//    donor of a cell lies in the same tree, so levels are separated by block
+//    barriers only -- the paper's private per-thread queues ("Independent
+//    Parallelism", RB+PQ) at the granularity of a thread block.  A block whose
+//    forest outgrows its queue share sets a flag and the whole step falls back
+//    to the device-wide form.
+//  * device-wide (stage-by-stage calls, and the fallback): one breadth-first
+//    queue for the whole grid, each level separated by a bounded grid barrier
+//    (the paper's "for-parallel" level loops), with runs of narrow levels
+//    handled by block 0 alone.  This form also produces the exported Queue and
+//    Levels in the oracle's breadth-first order.
 //
 // Data layout (all in HBM, row-major grid order unless stated):
 //   h      elevations (double or float), caller owned, updated in place
-//   code   u8  receiver code per cell (0..7 neighbour k, 8 none)
+//   code   u8  receiver code per cell (0..7 neighbour k, 8 pit, 9 perimeter)
 //   mask   u8  donor mask per cell: bit k set <=> neighbour k drains here
-//   queue  i32 cells in breadth-first order (Alg 3's Queue)
-//   levels i32 level offsets into queue (Alg 3's Levels), L+1 used
+//   queue  i32 cells in breadth-first order (device-wide form)
+//   levels i32 level offsets into queue, L+1 used
+//   pq     i32 block-private queues, `pcap` entries per block
 //   cnt    i32 or i64 cell counts (Alg 4's A in units of cells)
+//
+// FP64 on GB300 runs at about 1/70 of the FP32 rate, so the FP64 work per
+// cell is kept small: receivers compare elevations through their bit
+// patterns and evaluate only the two candidate slopes in FP64 (exact, see
+// receiver_code), and erosion divides by a tabulated reciprocal with one
+// FMA correction step instead of a full division.
 #pragma once
 
 #include "lem_device.cuh"
@@ -35,8 +57,10 @@ struct StepArgs {
   uint8_t* mask;
   int* queue;
   int* levels;
+  int* pq;              // block-private queues
+  int pcap;             // entries per block in pq
   CT* cnt;
-  const double* Ftab;   // F for counts < kTableN: [0,N) cardinal, [N,2N) diagonal
+  const double2* Ftab;  // {F, 1/(1+F)} for counts < kTableN: [0,N) cardinal, [N,2N) diagonal
   const float* gtab;    // F/(1+F) rounded to float, same layout
   DevState* st;
   int* partial;         // one int per block
@@ -45,21 +69,25 @@ struct StepArgs {
   int frozen;           // receivers frozen: codes are inputs, not recomputed
 };
 
-constexpr int kBD = 512;           // threads per block of the persistent kernel
-constexpr int kNarrow = 2 * kBD;   // a level this small is run by block 0 alone
+constexpr int kBD = 1024;          // threads per block: one block per SM
+constexpr int kWarps = kBD / 32;
+constexpr int kNarrow = kBD;       // a device-wide level this small runs in block 0
+constexpr int kItems = 4;          // items per thread per round in wide loops
+constexpr int kMaxPrivLevels = 2048;  // level offsets a private queue may hold
 
-// Alg 1 for one interior cell: steepest strictly positive descent, slope
-// compared as (h_c - h_n) * w in FP64 (w = 1 or 1/sqrt(2)), strict '>'
-// against an initial maximum of zero, so the lowest k wins ties.
-template <typename HT>
-__device__ __forceinline__ int receiver_code(const HT* __restrict__ h, int c, int nx) {
-  const double hc = (double)h[c];
+// ---- Alg 1: receivers ----------------------------------------------------------
+
+// Reference form: (h_c - h_n) * w in FP64 for all eight neighbours, strict
+// '>' against an initial maximum of zero (lowest k wins ties).
+__device__ __noinline__ int receiver_code_slow(double hc, double h0, double h1, double h2,
+                                               double h3, double h4, double h5, double h6,
+                                               double h7) {
+  const double hn[8] = {h0, h1, h2, h3, h4, h5, h6, h7};
   double smax = 0.0;
   int best = kSink;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const double hn = (double)h[c + nbr_off(k, nx)];
-    const double d = __dsub_rn(hc, hn);
+    const double d = __dsub_rn(hc, hn[k]);
     const double s = nbr_diag(k) ? __dmul_rn(d, kInvSqrt2) : d;
     if (s > smax) {
       smax = s;
@@ -69,38 +97,127 @@ __device__ __forceinline__ int receiver_code(const HT* __restrict__ h, int c, in
   return best;
 }
 
+// Bit-pattern view of non-negative finite elevations: for such values the
+// unsigned order of the patterns is the numeric order.
+template <typename HT> struct Bits;
+template <> struct Bits<double> {
+  using U = unsigned long long;
+  static constexpr U kInf = 0x7FF0000000000000ull;
+  static constexpr int kMant = 52;
+  static constexpr int kExpBias = 0;  // steps counted in doubles
+  __device__ static U of(double v) { return (U)__double_as_longlong(v); }
+};
+template <> struct Bits<float> {
+  using U = unsigned int;
+  static constexpr U kInf = 0x7F800000u;
+  static constexpr int kMant = 23;
+  static constexpr int kExpBias = 29;  // one float step spans 2^29 double steps
+  __device__ static U of(float v) { return (U)__float_as_uint(v); }
+};
+
+// True if no runner-up value r (> m, < hc) can produce the same rounded FP64
+// slope as the minimum m.  Two slopes fl(hc-a), or fl(fl(hc-a)*w), from a < b
+// can only coincide when b - a < 4 ulp(hc); b - a is at least (number of
+// representable steps from a to b) * (step at a), which bounds it from the
+// bit patterns and exponents alone.
+template <typename HT>
+__device__ __forceinline__ bool no_rounding_merge(typename Bits<HT>::U m, typename Bits<HT>::U r,
+                                                  typename Bits<HT>::U bc) {
+  using B = Bits<HT>;
+  if (r >= bc) return true;  // no second candidate below hc
+  const int Ec = (int)(bc >> B::kMant);
+  if (m == 0) {
+    // a = 0 gives the exact difference hc; b must reach 4 ulp(hc)
+    const int Er = (int)(r >> B::kMant);
+    return Er >= 1 && Er >= Ec - 50;
+  }
+  const int Em = max((int)(m >> B::kMant), 1);
+  const int sh = Ec - Em + 2 - B::kExpBias;
+  if (sh <= 0) return true;  // any distinct pair is far enough apart
+  if (sh > 62) return false;
+  return (unsigned long long)(r - m) >= (1ull << sh);
+}
+
+// Alg 1 for one interior cell.  Exactly the reference form's result: the
+// minimum elevation of each neighbour group (cardinal, diagonal) is found by
+// comparing bit patterns (lowest k among equal values), and only the two
+// group winners' slopes are evaluated in FP64 -- after checking that no other
+// neighbour of the group could round to the same slope.  Cells where that
+// check, or non-negative finiteness, fails take the reference form.
+template <typename HT>
+__device__ __forceinline__ int receiver_code(const HT* __restrict__ h, int c, int nx) {
+  using B = Bits<HT>;
+  using U = typename B::U;
+  HT v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = h[c + nbr_off(k, nx)];
+  const HT hcv = h[c];
+  const U bc = B::of(hcv);
+  U mC = bc, mD = bc, rC = bc, rD = bc;  // group minima and runners-up below hc
+  int kC = kSink, kD = kSink;
+  U worst = bc;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const U x = B::of(v[k]);
+    worst = x > worst ? x : worst;
+    if (nbr_diag(k)) {
+      if (x < mD) { rD = mD; mD = x; kD = k; }
+      else if (x > mD && x < rD) rD = x;
+    } else {
+      if (x < mC) { rC = mC; mC = x; kC = k; }
+      else if (x > mC && x < rC) rC = x;
+    }
+  }
+  if (worst < B::kInf && no_rounding_merge<HT>(mC, rC, bc) &&
+      no_rounding_merge<HT>(mD, rD, bc)) {
+    if (kC == kSink && kD == kSink) return kSink;
+    const double hc = (double)hcv;
+    if (kD == kSink) return kC;
+    const double sD = __dmul_rn(__dsub_rn(hc, (double)v[kD]), kInvSqrt2);
+    if (kC == kSink) return kD;
+    const double sC = __dsub_rn(hc, (double)v[kC]);
+    // both slopes are positive: compare their bit patterns
+    const long long bC = __double_as_longlong(sC), bD = __double_as_longlong(sD);
+    if (bC > bD) return kC;
+    if (bD > bC) return kD;
+    return min(kC, kD);
+  }
+  return receiver_code_slow((double)hcv, (double)v[0], (double)v[1], (double)v[2],
+                            (double)v[3], (double)v[4], (double)v[5], (double)v[6],
+                            (double)v[7]);
+}
+
 // Alg 2 for one cell (perimeter included): bit k set iff neighbour k is in
 // the grid and its receiver code points back at this cell (code 7-k).
 __device__ __forceinline__ int donor_mask(const uint8_t* __restrict__ code, int c, int x, int y,
                                           int nx, int ny) {
   int msk = 0;
+  if (x > 0 && y > 0 && x < nx - 1 && y < ny - 1) {
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int xn = x + nbr_dx(k), yn = y + nbr_dy(k);
-    if (xn >= 0 && yn >= 0 && xn < nx && yn < ny) {
+    for (int k = 0; k < 8; ++k)
       if (code[c + nbr_off(k, nx)] == 7 - k) msk |= 1 << k;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int xn = x + nbr_dx(k), yn = y + nbr_dy(k);
+      if (xn >= 0 && yn >= 0 && xn < nx && yn < ny)
+        if (code[c + nbr_off(k, nx)] == 7 - k) msk |= 1 << k;
     }
   }
   return msk;
 }
 
-template <typename HT, typename CT>
-__device__ __forceinline__ double erosion_F(const StepArgs<HT, CT>& a, CT count, bool diag) {
-  if (count < (CT)kTableN) return a.Ftab[(diag ? kTableN : 0) + (int)count];
-  const double A = __dmul_rn((double)count, a.area_scale);
-  return __ddiv_rn(__dmul_rn(a.Kdt, pow(A, a.m)), diag ? a.dxd : a.dx);
-}
+// ---- Alg 5 + Alg 6 -------------------------------------------------------------
 
 template <typename HT, typename CT>
 __device__ __forceinline__ double uplift_dt(const StepArgs<HT, CT>& a, int c) {
   return a.Uf ? __dmul_rn(a.Uf[c], a.dt) : __dmul_rn(a.U, a.dt);
 }
 
-// Alg 5 for a cell without receiver: uplift if interior.
+// Alg 5 for a cell without receiver: pits are uplifted, the perimeter is not.
 template <typename HT, typename CT>
 __device__ __forceinline__ void uplift_sink(const StepArgs<HT, CT>& a, int c) {
-  const int x = c % a.nx, y = c / a.nx;
-  if (x == 0 || y == 0 || x == a.nx - 1 || y == a.ny - 1) return;
+  if (a.code[c] != kSink) return;
   if constexpr (sizeof(HT) == 8) {
     a.h[c] = __dadd_rn(a.h[c], uplift_dt(a, c));
   } else {
@@ -108,42 +225,90 @@ __device__ __forceinline__ void uplift_sink(const StepArgs<HT, CT>& a, int c) {
   }
 }
 
-// Alg 5 + Alg 6 (n = 1) for one cell of level >= 1.
+// The n = 1 implicit update for one cell of level >= 1, given its receiver
+// code k, count, own elevation hcur and the receiver's updated elevation hr.
+// FP64: h = (h0 + F*hr)/(1+F) with h0 = h + dt*U.  The quotient is
+// q0 = num*inv (inv the correctly rounded 1/(1+F) from the table) refined
+// once by the FMA residual correction of Markstein (IBM J. Res. Dev. 34,
+// 1990): r = num - q0*(1+F) exactly, q = q0 + r*inv.
+// FP32: the increment form h0 - g*(h0 - hr), g = F/(1+F) from the table.
 template <typename HT, typename CT>
-__device__ __forceinline__ void erode_cell(const StepArgs<HT, CT>& a, int c) {
-  const int k = a.code[c];
-  const int r = c + nbr_off(k, a.nx);
-  const CT count = a.cnt[c];
+__device__ __forceinline__ HT erode_value(const StepArgs<HT, CT>& a, int c, int k, CT count,
+                                          HT hcur, HT hr) {
+  const bool diag = nbr_diag(k);
   if constexpr (sizeof(HT) == 8) {
-    const double F = erosion_F(a, count, nbr_diag(k));
-    const double h0 = __dadd_rn(a.h[c], uplift_dt(a, c));
-    const double num = __dadd_rn(h0, __dmul_rn(F, a.h[r]));
-    a.h[c] = __ddiv_rn(num, __dadd_rn(1.0, F));
+    const double h0 = __dadd_rn(hcur, uplift_dt(a, c));
+    if (count < (CT)kTableN) {
+      const double2 fi = a.Ftab[(diag ? kTableN : 0) + (int)count];
+      const double num = __dadd_rn(h0, __dmul_rn(fi.x, hr));
+      const double den = __dadd_rn(1.0, fi.x);
+      const double q0 = __dmul_rn(num, fi.y);
+      const double r = __fma_rn(-q0, den, num);
+      return __fma_rn(r, fi.y, q0);
+    }
+    const double A = __dmul_rn((double)count, a.area_scale);
+    const double F = __ddiv_rn(__dmul_rn(a.Kdt, pow(A, a.m)), diag ? a.dxd : a.dx);
+    const double num = __dadd_rn(h0, __dmul_rn(F, hr));
+    return __ddiv_rn(num, __dadd_rn(1.0, F));
   } else {
     float g;
     if (count < (CT)kTableN) {
-      g = a.gtab[(nbr_diag(k) ? kTableN : 0) + (int)count];
+      g = a.gtab[(diag ? kTableN : 0) + (int)count];
     } else {
-      const double F = erosion_F(a, count, nbr_diag(k));
+      const double A = (double)count * a.area_scale;
+      const double F = a.Kdt * pow(A, a.m) / (diag ? a.dxd : a.dx);
       g = (float)(F / (1.0 + F));
     }
-    const float h0 = __fadd_rn(a.h[c], (float)uplift_dt(a, c));
-    const float hr = a.h[r];
-    a.h[c] = __fmaf_rn(-g, __fsub_rn(h0, hr), h0);
+    const float h0 = __fadd_rn(hcur, (float)uplift_dt(a, c));
+    return __fmaf_rn(-g, __fsub_rn(h0, hr), h0);
   }
 }
 
-// Alg 4 for one cell: 1 + the donors' counts.
+// Erode up to kItems cells (entries < 0 are skipped) with all loads issued
+// before the arithmetic.
 template <typename HT, typename CT>
-__device__ __forceinline__ void accumulate_cell(const StepArgs<HT, CT>& a, int c) {
-  int msk = a.mask[c];
-  CT s = 1;
-  while (msk) {
-    const int k = __ffs(msk) - 1;
-    msk &= msk - 1;
-    s += a.cnt[c + nbr_off(k, a.nx)];
+__device__ __forceinline__ void erode_items(const StepArgs<HT, CT>& a, const int* cs) {
+  int ks[kItems];
+  CT ns[kItems];
+  HT hc[kItems], hr[kItems];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    if (cs[i] >= 0) {
+      ks[i] = a.code[cs[i]];
+      ns[i] = a.cnt[cs[i]];
+      hc[i] = a.h[cs[i]];
+    }
   }
-  a.cnt[c] = s;
+#pragma unroll
+  for (int i = 0; i < kItems; ++i)
+    if (cs[i] >= 0) hr[i] = a.h[cs[i] + nbr_off(ks[i], a.nx)];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i)
+    if (cs[i] >= 0) a.h[cs[i]] = erode_value(a, cs[i], ks[i], ns[i], hc[i], hr[i]);
+}
+
+// ---- Alg 4 ------------------------------------------------------------------------
+
+template <typename CT>
+__device__ __forceinline__ CT donor_sum(const CT* __restrict__ cnt, int c, int msk, int nx) {
+  CT s = 1;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if ((msk >> k) & 1) s += cnt[c + nbr_off(k, nx)];
+  return s;
+}
+
+template <typename HT, typename CT>
+__device__ __forceinline__ void accumulate_items(const StepArgs<HT, CT>& a, const int* cs) {
+  int ms[kItems];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) ms[i] = (cs[i] >= 0) ? a.mask[cs[i]] : 0;
+  CT s[kItems];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) s[i] = donor_sum(a.cnt, cs[i], ms[i], a.nx);
+#pragma unroll
+  for (int i = 0; i < kItems; ++i)
+    if (cs[i] >= 0) a.cnt[cs[i]] = s[i];
 }
 
 // Emit the donors of `c` (mask msk) at queue[pos...], k order.
@@ -156,218 +321,471 @@ __device__ __forceinline__ void emit_donors(int* __restrict__ queue, int pos, in
   }
 }
 
+// Sum of a per-block value over blocks [0, b) and over all blocks.
+template <int BD>
+__device__ __forceinline__ void block_prefix_of_partials(const int* partial, int G, int b,
+                                                         int* prefix, int* total,
+                                                         long long* s_sum) {
+  long long p = 0, s = 0;
+  for (int i = threadIdx.x; i < G; i += BD) {
+    const int v = partial[i];
+    s += v;
+    if (i < b) p += v;
+  }
+  *prefix = (int)block_sum<BD>(p, s_sum);
+  *total = (int)block_sum<BD>(s, s_sum);
+}
+
+struct Shared {
+  int scan[kWarps];
+  long long sum[kWarps];
+  int wcount[kWarps];
+  int plev[kMaxPrivLevels + 1];
+};
+
+// ---- phase: Alg 1 receivers, Alg 2 donor masks, level 0 of Alg 3 ---------------
+// Returns false if a barrier was abandoned.  On return *n0 holds the number
+// of this block's cells without receiver (its private level 0).
 template <typename HT, typename CT>
-__global__ void __launch_bounds__(kBD, 2) lem_step_kernel(StepArgs<HT, CT> a) {
+__device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& s, int* n0) {
+  const unsigned G = gridDim.x;
+  const int b = blockIdx.x, t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int nx = a.nx, ny = a.ny, N = a.N;
+  const int chunk = (N + (int)G - 1) / (int)G;
+  const int c0 = min(N, b * chunk), c1 = min(N, c0 + chunk);
+  const int wchunk = ((c1 - c0 + kWarps - 1) / kWarps + 31) & ~31;
+  const int w0 = min(c1, c0 + w * wchunk), w1 = min(c1, w0 + wchunk);
+  if (b == 0 && t == 0) a.st->private_overflow = 0;
+
+  // receiver codes and the count of cells without receiver, per warp
+  int wcnt = 0;
+  {
+    int x = w0 + lane, y = 0;
+    if (w0 < w1) {
+      y = x / nx;
+      x -= y * nx;
+    }
+    for (int base = w0; base < w1; base += 32) {
+      const int c = base + lane;
+      int code = kEdge;
+      if (c < w1) {
+        if (!a.frozen) {
+          const bool perim = (x == 0 || y == 0 || x == nx - 1 || y == ny - 1);
+          code = perim ? kEdge : receiver_code(a.h, c, nx);
+          a.code[c] = (uint8_t)code;
+        } else {
+          code = a.code[c];
+        }
+      }
+      wcnt += __popc(__ballot_sync(0xffffffffu, c < w1 && no_receiver(code)));
+      x += 32;
+      while (x >= nx) {
+        x -= nx;
+        ++y;
+      }
+    }
+  }
+  if (lane == 0) s.wcount[w] = wcnt;
+  __syncthreads();
+  if (t == 0) {
+    int tot = 0;
+    for (int i = 0; i < kWarps; ++i) tot += s.wcount[i];
+    a.partial[b] = tot;
+  }
+  if (!grid_barrier(a.st, G)) return false;
+  trace_point(a.st, kTrCodes);
+
+  int prefix, total;
+  block_prefix_of_partials<kBD>(a.partial, (int)G, b, &prefix, &total, s.sum);
+  int wpre = 0;
+  for (int i = 0; i < w; ++i) wpre += s.wcount[i];
+  int mine = 0;
+  for (int i = 0; i < kWarps; ++i) mine += s.wcount[i];
+  *n0 = mine;
+  // donor masks and the cells without receiver, ascending, into the global
+  // level 0 and this block's private level 0
+  int* pq = a.pq + (size_t)b * a.pcap;
+  {
+    int x = w0 + lane, y = 0;
+    if (w0 < w1) {
+      y = x / nx;
+      x -= y * nx;
+    }
+    int run = wpre;
+    for (int base = w0; base < w1; base += 32) {
+      const int c = base + lane;
+      bool f = false;
+      if (c < w1) {
+        a.mask[c] = (uint8_t)donor_mask(a.code, c, x, y, nx, ny);
+        f = no_receiver(a.code[c]);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (f) {
+        const int pos = run + __popc(bal & ((1u << lane) - 1u));
+        a.queue[prefix + pos] = c;
+        if (pos < a.pcap) pq[pos] = c;
+      }
+      run += __popc(bal);
+      x += 32;
+      while (x >= nx) {
+        x -= nx;
+        ++y;
+      }
+    }
+  }
+  if (b == 0 && t == 0) {
+    a.levels[0] = 0;
+    a.levels[1] = total;
+  }
+  if (!grid_barrier(a.st, G)) return false;
+  trace_point(a.st, kTrLevel0);
+  return true;
+}
+
+// ---- phase: device-wide Alg 3 ----------------------------------------------------
+// Returns the number of levels L, or -1 if a barrier was abandoned or the
+// receiver graph left cells unreached (a cycle; recorded as kErrInval).
+template <typename HT, typename CT>
+__device__ __noinline__ int phase_global_levels(const StepArgs<HT, CT>& a, Shared& s) {
+  const unsigned G = gridDim.x;
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int nx = a.nx;
+  int lo = 0, hi = a.levels[1], l = 0;
+  while (true) {
+    const int S = hi - lo;
+    if (S <= kNarrow) {
+      if (b == 0) {
+        // block 0 alone: consecutive narrow levels, block barriers only
+        bool done = false;
+        while (true) {
+          int run = hi;
+          for (int base = lo; base < hi; base += kBD) {
+            const int j = base + t;
+            int c = 0, msk = 0;
+            if (j < hi) {
+              c = a.queue[j];
+              msk = a.mask[c];
+            }
+            int tot;
+            const int ex = block_exclusive_scan<kBD>(__popc(msk), &tot, s.scan);
+            if (msk) emit_donors(a.queue, run + ex, c, msk, nx);
+            run += tot;
+          }
+          __syncthreads();
+          if (t == 0) a.levels[l + 2] = run;
+          if (run == hi) {
+            done = true;
+            break;
+          }
+          lo = hi;
+          hi = run;
+          ++l;
+          if (hi - lo > kNarrow) break;
+        }
+        if (t == 0) {
+          a.st->bfs_lo = lo;
+          a.st->bfs_hi = hi;
+          a.st->bfs_level = l;
+          a.st->bfs_done = done ? 1 : 0;
+        }
+      }
+      if (!grid_barrier(a.st, G)) return -1;
+      trace_point(a.st, kTrBfsNarrow + l);
+      lo = ld_volatile(&a.st->bfs_lo);
+      hi = ld_volatile(&a.st->bfs_hi);
+      l = ld_volatile(&a.st->bfs_level);
+      if (ld_volatile(&a.st->bfs_done)) break;
+      continue;
+    }
+    // wide level: each block owns a contiguous chunk of the frontier;
+    // every thread takes kItems consecutive entries per round.
+    const int chunk = (S + (int)G - 1) / (int)G;
+    const int j0 = min(hi, lo + b * chunk), j1 = min(hi, j0 + chunk);
+    long long nd = 0;
+    for (int base = j0 + kItems * t; base < j1; base += kItems * kBD) {
+      int cs[kItems];
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) cs[i] = (base + i < j1) ? a.queue[base + i] : -1;
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) nd += (cs[i] >= 0) ? __popc(a.mask[cs[i]]) : 0;
+    }
+    nd = block_sum<kBD>(nd, s.sum);
+    if (t == 0) a.partial[b] = (int)nd;
+    if (!grid_barrier(a.st, G)) return -1;
+    int prefix, total;
+    block_prefix_of_partials<kBD>(a.partial, (int)G, b, &prefix, &total, s.sum);
+    int run = hi + prefix;
+    for (int base0 = j0; base0 < j1; base0 += kItems * kBD) {
+      const int base = base0 + kItems * t;
+      int cs[kItems], ms[kItems];
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) cs[i] = (base + i < j1) ? a.queue[base + i] : -1;
+      int mine = 0;
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        ms[i] = (cs[i] >= 0) ? a.mask[cs[i]] : 0;
+        mine += __popc(ms[i]);
+      }
+      int tot;
+      int pos = run + block_exclusive_scan<kBD>(mine, &tot, s.scan);
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        if (ms[i]) {
+          emit_donors(a.queue, pos, cs[i], ms[i], nx);
+          pos += __popc(ms[i]);
+        }
+      }
+      run += tot;
+    }
+    if (b == 0 && t == 0) a.levels[l + 2] = hi + total;
+    if (!grid_barrier(a.st, G)) return -1;
+    trace_point(a.st, kTrBfsWide + l);
+    if (total == 0) break;
+    lo = hi;
+    hi = hi + total;
+    ++l;
+  }
+  // L = l + 1 levels; every cell must have been reached
+  const int L = l + 1;
+  if (b == 0 && t == 0) a.st->nlevels = L;
+  if (a.levels[L] != a.N) {
+    if (b == 0 && t == 0) set_error(a.st, kErrInval);
+    return -1;
+  }
+  return L;
+}
+
+// ---- phase: device-wide Alg 4 ----------------------------------------------------
+template <typename HT, typename CT>
+__device__ __noinline__ bool phase_global_accumulate(const StepArgs<HT, CT>& a, int L) {
   const unsigned G = gridDim.x;
   const int b = blockIdx.x, t = threadIdx.x;
   const int gtid = b * kBD + t, gstride = (int)G * kBD;
-  const int nx = a.nx, ny = a.ny, N = a.N;
-  __shared__ int s_scan[kBD / 32];
-  __shared__ long long s_sum[kBD / 32];
+  int l = L - 1;
+  while (l >= 0) {
+    int lo = a.levels[l], hi = a.levels[l + 1];
+    if (hi - lo <= kNarrow) {
+      int ll = l;
+      if (b == 0) {
+        while (ll >= 0) {
+          lo = a.levels[ll];
+          hi = a.levels[ll + 1];
+          if (hi - lo > kNarrow) break;
+          for (int j = lo + t; j < hi; j += kBD) {
+            const int c = a.queue[j];
+            a.cnt[c] = donor_sum(a.cnt, c, a.mask[c], a.nx);
+          }
+          __syncthreads();
+          --ll;
+        }
+      } else {
+        while (ll >= 0 && a.levels[ll + 1] - a.levels[ll] <= kNarrow) --ll;
+      }
+      if (!grid_barrier(a.st, G)) return false;
+      trace_point(a.st, kTrAccNarrow + ll + 1);
+      l = ll;
+      continue;
+    }
+    for (int base = lo + gtid; base < hi; base += kItems * gstride) {
+      int cs[kItems];
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        const int j = base + i * gstride;
+        cs[i] = (j < hi) ? a.queue[j] : -1;
+      }
+      accumulate_items(a, cs);
+    }
+    if (!grid_barrier(a.st, G)) return false;
+    trace_point(a.st, kTrAccWide + l);
+    --l;
+  }
+  return true;
+}
+
+// ---- phase: device-wide Algs 5-6 ---------------------------------------------------
+template <typename HT, typename CT>
+__device__ __noinline__ bool phase_global_erode(const StepArgs<HT, CT>& a, int L) {
+  const unsigned G = gridDim.x;
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int gtid = b * kBD + t, gstride = (int)G * kBD;
+  for (int j = gtid; j < a.levels[1]; j += gstride) uplift_sink(a, a.queue[j]);
+  if (!grid_barrier(a.st, G)) return false;
+  trace_point(a.st, kTrUplift);
+  int l = 1;
+  while (l < L) {
+    int lo = a.levels[l], hi = a.levels[l + 1];
+    if (hi - lo <= kNarrow) {
+      int ll = l;
+      if (b == 0) {
+        while (ll < L) {
+          lo = a.levels[ll];
+          hi = a.levels[ll + 1];
+          if (hi - lo > kNarrow) break;
+          for (int j = lo + t; j < hi; j += kBD) {
+            int cs[kItems] = {a.queue[j], -1, -1, -1};
+            erode_items(a, cs);
+          }
+          __syncthreads();
+          ++ll;
+        }
+      } else {
+        while (ll < L && a.levels[ll + 1] - a.levels[ll] <= kNarrow) ++ll;
+      }
+      if (!grid_barrier(a.st, G)) return false;
+      trace_point(a.st, kTrEroNarrow + ll);
+      l = ll;
+      continue;
+    }
+    for (int base = lo + gtid; base < hi; base += kItems * gstride) {
+      int cs[kItems];
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        const int j = base + i * gstride;
+        cs[i] = (j < hi) ? a.queue[j] : -1;
+      }
+      erode_items(a, cs);
+    }
+    if (!grid_barrier(a.st, G)) return false;
+    trace_point(a.st, kTrEroWide + l);
+    ++l;
+  }
+  return true;
+}
+
+// ---- phase: block-private Algs 3-6 -------------------------------------------------
+// Returns 1 if done privately, 0 if the step must fall back to the
+// device-wide form, -1 if a barrier was abandoned.
+template <typename HT, typename CT>
+__device__ __noinline__ int phase_private(const StepArgs<HT, CT>& a, Shared& s, int n0) {
+  const unsigned G = gridDim.x;
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int nx = a.nx;
+  int* pq = a.pq + (size_t)b * a.pcap;
+  // Alg 3 on this block's trees
+  bool ovf = n0 > a.pcap;
+  int lo = 0, hi = n0, PL = 1;
+  if (t == 0) {
+    s.plev[0] = 0;
+    s.plev[1] = n0;
+  }
+  while (!ovf && lo < hi) {
+    int run = hi;
+    for (int base0 = lo; base0 < hi; base0 += kItems * kBD) {
+      const int base = base0 + kItems * t;
+      int cs[kItems], ms[kItems];
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) cs[i] = (base + i < hi) ? pq[base + i] : -1;
+      int mine = 0;
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        ms[i] = (cs[i] >= 0) ? a.mask[cs[i]] : 0;
+        mine += __popc(ms[i]);
+      }
+      int tot;
+      int pos = run + block_exclusive_scan<kBD>(mine, &tot, s.scan);
+      if (run + tot > a.pcap) {
+        ovf = true;
+        break;
+      }
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        if (ms[i]) {
+          emit_donors(pq, pos, cs[i], ms[i], nx);
+          pos += __popc(ms[i]);
+        }
+      }
+      run += tot;
+    }
+    __syncthreads();
+    if (ovf || run == hi) break;
+    if (PL >= kMaxPrivLevels) {
+      ovf = true;
+      break;
+    }
+    ++PL;
+    if (t == 0) s.plev[PL] = run;
+    lo = hi;
+    hi = run;
+  }
+  if (ovf && t == 0) a.st->private_overflow = 1;
+  if (!grid_barrier(a.st, G)) return -1;
+  trace_point(a.st, kTrPrivBfs);
+  if (ld_volatile(&a.st->private_overflow)) return 0;
+
+  // Alg 4, this block's levels from the highest down
+  for (int l = PL - 1; l >= 0; --l) {
+    const int l0 = s.plev[l], l1 = s.plev[l + 1];
+    for (int base = l0 + t; base < l1; base += kItems * kBD) {
+      int cs[kItems];
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        const int j = base + i * kBD;
+        cs[i] = (j < l1) ? pq[j] : -1;
+      }
+      accumulate_items(a, cs);
+    }
+    __syncthreads();
+  }
+  trace_point(a.st, kTrPrivAcc);
+  // Alg 5 on level 0, then Alg 6 from level 1 up
+  for (int j = t; j < s.plev[1]; j += kBD) uplift_sink(a, pq[j]);
+  __syncthreads();
+  for (int l = 1; l < PL; ++l) {
+    const int l0 = s.plev[l], l1 = s.plev[l + 1];
+    for (int base = l0 + t; base < l1; base += kItems * kBD) {
+      int cs[kItems];
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        const int j = base + i * kBD;
+        cs[i] = (j < l1) ? pq[j] : -1;
+      }
+      erode_items(a, cs);
+    }
+    __syncthreads();
+  }
+  trace_point(a.st, kTrPrivEro);
+  return 1;
+}
+
+template <typename HT, typename CT>
+__global__ void __launch_bounds__(kBD, 1) lem_step_kernel(StepArgs<HT, CT> a) {
+  __shared__ Shared s;
+  const unsigned G = gridDim.x;
 
   for (int step = 0; step < a.nsteps; ++step) {
-    int L_here = -1;  // L found by this launch's Alg 3 phase
-    // ---- Alg 1 receivers, Alg 2 donor masks, level 0 of Alg 3 ------------
-    if (a.phases & kPhRec) {
-      if (!a.frozen) {
-        for (int c = gtid; c < N; c += gstride) {
-          const int x = c % nx, y = c / nx;
-          const bool perim = (x == 0 || y == 0 || x == nx - 1 || y == ny - 1);
-          a.code[c] = (uint8_t)(perim ? kSink : receiver_code(a.h, c, nx));
-        }
+    trace_point(a.st, kTrStart + step);
+    int n0 = 0;
+    if (a.phases & kPhRec)
+      if (!phase_receivers(a, s, &n0)) return;
+
+    if (a.phases & kPhPrivate) {
+      const int r = phase_private(a, s, n0);
+      if (r < 0) return;
+      if (r == 0) {
+        const int L = phase_global_levels(a, s);
+        if (L < 0) return;
+        if (!phase_global_accumulate(a, L)) return;
+        if (!phase_global_erode(a, L)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.st->global_steps += 1;
+      } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.st->private_steps += 1;
+      }
+      if (step + 1 < a.nsteps) {
         if (!grid_barrier(a.st, G)) return;
+        trace_point(a.st, kTrStepEnd);
       }
-      // Each block owns one contiguous chunk: donor masks, then the sinks of
-      // the chunk in ascending address order.
-      const int chunk = (N + (int)G - 1) / (int)G;
-      const int c0 = min(N, b * chunk), c1 = min(N, c0 + chunk);
-      long long nsink = 0;
-      for (int c = c0 + t; c < c1; c += kBD) {
-        const int x = c % nx, y = c / nx;
-        a.mask[c] = (uint8_t)donor_mask(a.code, c, x, y, nx, ny);
-        nsink += (a.code[c] == kSink);
-      }
-      nsink = block_sum<kBD>(nsink, s_sum);
-      if (t == 0) a.partial[b] = (int)nsink;
-      if (!grid_barrier(a.st, G)) return;
-      int prefix = 0, total = 0;
-      for (int i = t; i < (int)G; i += kBD) {
-        const int v = a.partial[i];
-        total += v;
-        if (i < b) prefix += v;
-      }
-      prefix = (int)block_sum<kBD>(prefix, s_sum);
-      total = (int)block_sum<kBD>(total, s_sum);
-      int run = prefix;
-      for (int base = c0; base < c1; base += kBD) {
-        const int c = base + t;
-        const int f = (c < c1) && (a.code[c] == kSink);
-        int tot;
-        const int ex = block_exclusive_scan<kBD>(f, &tot, s_scan);
-        if (f) a.queue[run + ex] = c;
-        run += tot;
-      }
-      if (b == 0 && t == 0) {
-        a.levels[0] = 0;
-        a.levels[1] = total;
-      }
-      if (!grid_barrier(a.st, G)) return;
+      continue;
     }
 
-    // ---- Alg 3: breadth-first levels -------------------------------------
+    int L = -1;
     if (a.phases & kPhLev) {
-      int lo = 0, hi = a.levels[1], l = 0;
-      while (true) {
-        const int S = hi - lo;
-        if (S <= kNarrow) {
-          if (b == 0) {
-            // block 0 alone: consecutive narrow levels, block barriers only
-            bool done = false;
-            while (true) {
-              int run = hi;
-              for (int base = lo; base < hi; base += kBD) {
-                const int j = base + t;
-                int c = 0, msk = 0;
-                if (j < hi) {
-                  c = a.queue[j];
-                  msk = a.mask[c];
-                }
-                int tot;
-                const int ex = block_exclusive_scan<kBD>(__popc(msk), &tot, s_scan);
-                if (msk) emit_donors(a.queue, run + ex, c, msk, nx);
-                run += tot;
-              }
-              __syncthreads();
-              if (t == 0) a.levels[l + 2] = run;
-              if (run == hi) {
-                done = true;
-                break;
-              }
-              lo = hi;
-              hi = run;
-              ++l;
-              if (hi - lo > kNarrow) break;
-            }
-            if (t == 0) {
-              a.st->bfs_lo = lo;
-              a.st->bfs_hi = hi;
-              a.st->bfs_level = l;
-              a.st->bfs_done = done ? 1 : 0;
-            }
-          }
-          if (!grid_barrier(a.st, G)) return;
-          lo = ld_volatile(&a.st->bfs_lo);
-          hi = ld_volatile(&a.st->bfs_hi);
-          l = ld_volatile(&a.st->bfs_level);
-          if (ld_volatile(&a.st->bfs_done)) break;
-          continue;
-        }
-        // wide level: count, barrier, deterministic offsets, write, barrier
-        const int chunk = (S + (int)G - 1) / (int)G;
-        const int j0 = min(hi, lo + b * chunk), j1 = min(hi, j0 + chunk);
-        long long nd = 0;
-        for (int j = j0 + t; j < j1; j += kBD) nd += __popc(a.mask[a.queue[j]]);
-        nd = block_sum<kBD>(nd, s_sum);
-        if (t == 0) a.partial[b] = (int)nd;
-        if (!grid_barrier(a.st, G)) return;
-        int prefix = 0, total = 0;
-        for (int i = t; i < (int)G; i += kBD) {
-          const int v = a.partial[i];
-          total += v;
-          if (i < b) prefix += v;
-        }
-        prefix = (int)block_sum<kBD>(prefix, s_sum);
-        total = (int)block_sum<kBD>(total, s_sum);
-        int run = hi + prefix;
-        for (int base = j0; base < j1; base += kBD) {
-          const int j = base + t;
-          int c = 0, msk = 0;
-          if (j < j1) {
-            c = a.queue[j];
-            msk = a.mask[c];
-          }
-          int tot;
-          const int ex = block_exclusive_scan<kBD>(__popc(msk), &tot, s_scan);
-          if (msk) emit_donors(a.queue, run + ex, c, msk, nx);
-          run += tot;
-        }
-        if (b == 0 && t == 0) a.levels[l + 2] = hi + total;
-        if (!grid_barrier(a.st, G)) return;
-        if (total == 0) break;
-        lo = hi;
-        hi = hi + total;
-        ++l;
-      }
-      // L = l + 1 levels; every cell must have been reached
-      const int L = l + 1;
-      L_here = L;
-      if (b == 0 && t == 0) a.st->nlevels = L;
-      if (a.levels[L] != N) {
-        if (b == 0 && t == 0) set_error(a.st, kErrInval);
-        return;
-      }
+      L = phase_global_levels(a, s);
+      if (L < 0) return;
     }
-
-    const int L = L_here >= 0 ? L_here : ld_volatile(&a.st->nlevels);
-
-    // ---- Alg 4: accumulation, highest level down --------------------------
-    if (a.phases & kPhAcc) {
-      int l = L - 1;
-      while (l >= 0) {
-        int lo = a.levels[l], hi = a.levels[l + 1];
-        if (hi - lo <= kNarrow) {
-          int ll = l;
-          if (b == 0) {
-            while (ll >= 0) {
-              lo = a.levels[ll];
-              hi = a.levels[ll + 1];
-              if (hi - lo > kNarrow) break;
-              for (int j = lo + t; j < hi; j += kBD) accumulate_cell(a, a.queue[j]);
-              __syncthreads();
-              --ll;
-            }
-          } else {
-            while (ll >= 0 && a.levels[ll + 1] - a.levels[ll] <= kNarrow) --ll;
-          }
-          if (!grid_barrier(a.st, G)) return;
-          l = ll;
-          continue;
-        }
-        for (int j = lo + gtid; j < hi; j += gstride) accumulate_cell(a, a.queue[j]);
-        if (!grid_barrier(a.st, G)) return;
-        --l;
-      }
-    }
-
-    // ---- Alg 5 + Alg 6: uplift and erosion, level 1 upward ------------------
-    if (a.phases & kPhEro) {
-      for (int j = gtid; j < a.levels[1]; j += gstride) uplift_sink(a, a.queue[j]);
-      if (!grid_barrier(a.st, G)) return;
-      int l = 1;
-      while (l < L) {
-        int lo = a.levels[l], hi = a.levels[l + 1];
-        if (hi - lo <= kNarrow) {
-          int ll = l;
-          if (b == 0) {
-            while (ll < L) {
-              lo = a.levels[ll];
-              hi = a.levels[ll + 1];
-              if (hi - lo > kNarrow) break;
-              for (int j = lo + t; j < hi; j += kBD) erode_cell(a, a.queue[j]);
-              __syncthreads();
-              ++ll;
-            }
-          } else {
-            while (ll < L && a.levels[ll + 1] - a.levels[ll] <= kNarrow) ++ll;
-          }
-          if (!grid_barrier(a.st, G)) return;
-          l = ll;
-          continue;
-        }
-        for (int j = lo + gtid; j < hi; j += gstride) erode_cell(a, a.queue[j]);
-        if (!grid_barrier(a.st, G)) return;
-        ++l;
-      }
+    if (a.phases & (kPhAcc | kPhEro)) {
+      if (L < 0) L = ld_volatile(&a.st->nlevels);
+      if ((a.phases & kPhAcc) && !phase_global_accumulate(a, L)) return;
+      if ((a.phases & kPhEro) && !phase_global_erode(a, L)) return;
     }
   }
 }

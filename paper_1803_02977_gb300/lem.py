@@ -53,8 +53,17 @@ SIGNATURES = [
     ("lem_sync", _I, [_VP]),
     ("lem_set_wait_limit", _I, [_VP, _D]),
     ("lem_selftest_wait", _I, [_VP]),
+    ("lem_set_step_mode", _I, [_VP, _I]),
+    ("lem_step_stats", _I, [_VP, _I64P, _I64P]),
+    ("lem_trace_enable", _I, [_VP, _I]),
+    ("lem_trace_read", _I, [_VP, _VP, _VP, _I, ctypes.POINTER(_I)]),
     ("lem_status_string", ctypes.c_char_p, [_I]),
 ]
+
+TRACE_PHASES = {1: "start", 2: "receivers", 3: "level0", 4: "bfs_wide", 5: "bfs_narrow",
+                6: "acc_wide", 7: "acc_narrow", 8: "uplift", 9: "erode_wide",
+                10: "erode_narrow", 11: "private_levels", 12: "private_accumulate",
+                13: "private_erode", 14: "step_end"}
 
 
 def lib(build_if_missing: bool = True):
@@ -164,6 +173,34 @@ def lem_set_wait_limit(ctx, seconds):
 def lem_selftest_wait(ctx):
     """Returns the raw status (LEM_ETIMEOUT expected)."""
     return lib().lem_selftest_wait(ctx)
+
+
+def lem_set_step_mode(ctx, mode):
+    _check(lib().lem_set_step_mode(ctx, mode), "lem_set_step_mode")
+
+
+def lem_step_stats(ctx):
+    """(steps on block-private queues, steps on device-wide levels)."""
+    p, g = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().lem_step_stats(ctx, ctypes.byref(p), ctypes.byref(g)), "lem_step_stats")
+    return p.value, g.value
+
+
+def lem_trace_enable(ctx, capacity):
+    _check(lib().lem_trace_enable(ctx, capacity), "lem_trace_enable")
+
+
+def lem_trace_read(ctx, cap=4096):
+    """Returns a list of (ns, phase name, level) recorded since the last read."""
+    import numpy as np
+    ns = np.zeros(cap, np.int64)
+    tags = np.zeros(cap, np.int32)
+    n = ctypes.c_int(0)
+    _check(lib().lem_trace_read(ctx, ns.ctypes.data_as(_VP), tags.ctypes.data_as(_VP), cap,
+                                ctypes.byref(n)), "lem_trace_read")
+    m = min(n.value, cap)
+    return [(int(ns[i]), TRACE_PHASES.get(int(tags[i]) >> 16, "?"), int(tags[i]) & 0xFFFF)
+            for i in range(m)]
 
 
 # ---- convenience wrapper ------------------------------------------------------

@@ -89,6 +89,44 @@ def test_stages_fp64_bit_exact_and_tolerance(name, make):
     assert np.abs(g["h"] - want).max() <= REL64 * scale
 
 
+def _adversarial(kind, nx, ny, seed):
+    """Surfaces built to provoke FP64 rounding collisions between slopes."""
+    rng = np.random.default_rng(seed)
+    if kind == "tiny_next_to_large":
+        h = rng.random((ny, nx)) * 2.0 ** -60
+        h[1::3, 1::3] = 1.0 + rng.random(h[1::3, 1::3].shape)
+    elif kind == "few_ulps":
+        base = 1.0 + rng.random()
+        h = base + rng.integers(0, 6, (ny, nx)) * np.spacing(base)
+    elif kind == "mixed_zeros":
+        h = rng.choice([0.0, 1e-300, 5e-324, 1e-17, 0.5, 1.0, 3.0], (ny, nx))
+    elif kind == "low_bits":
+        h = np.full((ny, nx), 1e-20) + rng.integers(0, 3, (ny, nx)) * 1e-36
+        h[1::4, 1::4] = 1e3
+    else:  # "negative_and_nan": the exact reference form handles these cells
+        h = rng.random((ny, nx)) - 0.5
+        h[rng.random((ny, nx)) < 0.01] = np.nan
+        h[rng.random((ny, nx)) < 0.01] = -0.0
+    return h
+
+
+@pytest.mark.parametrize("kind", ["tiny_next_to_large", "few_ulps", "mixed_zeros", "low_bits",
+                                  "negative_and_nan"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_receivers_adversarial_rounding(kind, dtype):
+    lem = _lem()
+    dev = _dev()
+    h0 = _adversarial(kind, 211, 157, 7)
+    if dtype == "f32":
+        h0 = h0.astype(np.float32)
+    h = torch.tensor(h0, device=dev)
+    mdl = lem.Model(h)
+    rec = mdl.receivers().cpu().numpy()
+    mdl.sync()
+    mdl.close()
+    assert np.array_equal(rec, oracle.receivers(h0))
+
+
 def test_stages_int64_counts():
     h0 = synth.noise_surface(300, 211, 9)
     g = _run_stages(h0, count_bits=64)
@@ -134,6 +172,60 @@ def test_step_matches_oracle_per_step():
     assert torch.equal(h, h2)
     mdl.close()
     m2.close()
+
+
+STEP_CASES = [
+    ("noise_256", lambda: synth.noise_surface(256, 256, 1), "private"),
+    ("noise_tilt_700x500", lambda: synth.noise_surface(700, 500, 3, south_tilt=1e-4), "private"),
+    ("int_300x300", lambda: _int_grid(300, 300, 9, levels=12), "private"),
+    # one long chain per row (about 1500 private levels each)
+    ("tilted_1500x64", lambda: _tilted(1500, 64, 7, slope=0.2), "private"),
+    # a cone draining the whole grid to one outlet: that block's forest
+    # outgrows its private share and the step falls back to device-wide levels
+    ("cone_300x300", lambda: _cone(300, 300, 11), "fallback"),
+]
+
+
+def _cone(nx, ny, seed):
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    cy = ny // 2
+    h = 100.0 * np.hypot(x, y - cy) + 0.01 * synth.uniform01(seed, nx * ny).reshape(ny, nx)
+    h[0, :] = h[-1, :] = h[:, 0] = h[:, -1] = 1e6  # raised rim ...
+    h[cy, 0] = 0.0                                 # ... but for one outlet
+    return h
+
+
+@pytest.mark.parametrize("name,make,path", STEP_CASES, ids=[c[0] for c in STEP_CASES])
+def test_step_modes_match_oracle_and_each_other(name, make, path):
+    lem = _lem()
+    dev = _dev()
+    h0 = make()
+    par = dict(dx=100.0, K=2e-5, m=0.5, U=1e-3, dt=1000.0)
+    p = oracle.params(**par)
+    hs = {}
+    for mode in (0, 1):
+        h = torch.tensor(h0, device=dev)
+        mdl = lem.Model(h, **par)
+        lem.lem_set_step_mode(mdl.ctx, mode)
+        cur = h0.copy()
+        for _ in range(4):
+            mdl.step(1)
+            mdl.sync()
+            want, _ = oracle.step(cur, p)
+            got = h.cpu().numpy()
+            assert np.abs(got - want).max() <= REL64 * max(np.abs(want).max(), 1.0)
+            cur = got
+        priv, wide = lem.lem_step_stats(mdl.ctx)
+        if mode == 1:
+            assert (priv, wide) == (0, 0)  # device-wide mode does not use the private form
+        elif path == "private":
+            assert priv == 4 and wide == 0
+        else:
+            assert wide >= 1
+        hs[mode] = h.cpu().numpy()
+        mdl.close()
+    # same per-cell arithmetic in both forms: identical elevations
+    assert np.array_equal(hs[0], hs[1])
 
 
 def test_uplift_field():
