@@ -200,6 +200,34 @@ LEM_API int lem_trace_enable(lem_ctx* ctx, int capacity);
  * 10 narrow erosion. */
 LEM_API int lem_trace_read(lem_ctx* ctx, int64_t* ns, int32_t* tags, int cap, int* n);
 
+/* Largest grid (nx*ny cells) accepted by lem_step_noalloc. */
+#define LEM_NOALLOC_MAX_CELLS (1 << 18)
+
+/* Allocation-free form of lem_step, for callers that must not allocate
+ * device memory -- for instance code embedded in a framework whose caching
+ * allocator owns the GPU's memory, or a latency-critical loop where
+ * cudaMalloc/cudaFree are off limits because they may block and implicitly
+ * synchronise the device.  The paper has no counterpart: this is a
+ * deployment convenience around the same step kernel.
+ *
+ * Runs nsteps FP64 steps (32-bit counts, area = dx*dx, scalar uplift) on the
+ * caller's device array dev_h (nx*ny doubles, updated in place) on `stream`
+ * (a cudaStream_t, NULL = legacy default), then synchronises that stream and
+ * returns the kernel's status.  No context is created and nothing is
+ * allocated or freed: the working memory is one fixed array of about 10 MiB
+ * in the library's device image, held by every GPU that loads the library
+ * until the process exits.
+ *  - Grids with nx*ny > LEM_NOALLOC_MAX_CELLS (or nx, ny < 3, or invalid
+ *    parameters) are rejected with LEM_EINVAL before any device work.
+ *  - The first call on each device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; each call clears what must start at zero.  Calls that overlap on
+ *    the GPU (from two host threads or two streams) race on it: serialise
+ *    them. */
+LEM_API int lem_step_noalloc(int nx, int ny, double* dev_h, double dx, double K, double m,
+                             double U, double dt, int nsteps, void* stream);
+
 /* Static description of a status code. */
 LEM_API const char* lem_status_string(int status);
 

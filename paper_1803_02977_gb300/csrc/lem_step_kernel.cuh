@@ -79,7 +79,7 @@ constexpr int kMaxPrivLevels = 2048;  // level offsets a private queue may hold
 
 // Reference form: (h_c - h_n) * w in FP64 for all eight neighbours, strict
 // '>' against an initial maximum of zero (lowest k wins ties).
-__device__ __noinline__ int receiver_code_slow(double hc, double h0, double h1, double h2,
+static __device__ __noinline__ int receiver_code_slow(double hc, double h0, double h1, double h2,
                                                double h3, double h4, double h5, double h6,
                                                double h7) {
   const double hn[8] = {h0, h1, h2, h3, h4, h5, h6, h7};

@@ -57,8 +57,11 @@ SIGNATURES = [
     ("lem_step_stats", _I, [_VP, _I64P, _I64P]),
     ("lem_trace_enable", _I, [_VP, _I]),
     ("lem_trace_read", _I, [_VP, _VP, _VP, _I, ctypes.POINTER(_I)]),
+    ("lem_step_noalloc", _I, [_I, _I, _VP, _D, _D, _D, _D, _D, _I, _VP]),
     ("lem_status_string", ctypes.c_char_p, [_I]),
 ]
+
+LEM_NOALLOC_MAX_CELLS = 1 << 18
 
 TRACE_PHASES = {1: "start", 2: "receivers", 3: "level0", 4: "bfs_wide", 5: "bfs_narrow",
                 6: "acc_wide", 7: "acc_narrow", 8: "uplift", 9: "erode_wide",
@@ -184,6 +187,16 @@ def lem_step_stats(ctx):
     p, g = ctypes.c_int64(0), ctypes.c_int64(0)
     _check(lib().lem_step_stats(ctx, ctypes.byref(p), ctypes.byref(g)), "lem_step_stats")
     return p.value, g.value
+
+
+def lem_step_noalloc(h, dx, K, m, U, dt, nsteps, stream=None):
+    """Allocation-free steps on a (ny, nx) float64 CUDA tensor; returns the raw
+    status (the library allocates nothing: see include/lem.h)."""
+    if h.dtype != torch.float64:
+        raise ValueError("lem_step_noalloc takes float64 elevations")
+    ny, nx = h.shape
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    return lib().lem_step_noalloc(nx, ny, _ptr(h), dx, K, m, U, dt, nsteps, ctypes.c_void_p(s))
 
 
 def lem_trace_enable(ctx, capacity):
