@@ -386,14 +386,18 @@ def traced_step(lem, mdl, flush):
              "private_erode": "erode", "step_end": "erode"}
     out = {"receivers": 0.0, "levels": 0.0, "accumulate": 0.0, "erode": 0.0}
     barriers = {"wide_levels": 0, "narrow_runs": 0}
-    for (t0, _, _), (t1, ph, _) in zip(tr[:-1], tr[1:]):
-        out[group.get(ph, "receivers")] += (t1 - t0) / 1e3
+    for (t0, _, _), (t1, ph, lvl) in zip(tr[:-1], tr[1:]):
+        if ph == "block0_done":  # block 0 reached barrier 1, 2 (receivers) or 3 (levels)
+            ph = "levels" if lvl == 3 else "receivers"
+        out[group.get(ph, ph if ph in out else "receivers")] += (t1 - t0) / 1e3
         if ph.endswith("_wide"):
             barriers["wide_levels"] += 1
         elif ph.endswith("_narrow"):
             barriers["narrow_runs"] += 1
+    raw = [[ph, lvl, round((t1 - t0) / 1e3, 2)]
+           for (t0, _, _), (t1, ph, lvl) in zip(tr[:-1], tr[1:])][:64]
     return {"us": out, "total_us": (tr[-1][0] - tr[0][0]) / 1e3, "segments": len(tr) - 1,
-            **barriers}
+            **barriers, "raw": raw}
 
 
 def measured_peaks():

@@ -141,8 +141,10 @@ LEM_API int lem_accumulate(lem_ctx* ctx, void* dev_counts);
  * receiver are uplifted, h += dt*U; then, level 1 upward, every cell takes
  * h = (h + dt*U + F*h_r) / (1 + F), F = K*dt*(count*area_scale)^m / d,
  * d = dx (cardinal receiver) or dx*sqrt(2) (diagonal), h_r the receiver's
- * updated elevation.  FP32 contexts evaluate the same update in the
- * increment form h0 - g*(h0 - h_r), g = F/(1+F) rounded once from FP64.
+ * updated elevation.  The update is evaluated in the algebraically identical
+ * increment form h0 - g*(h0 - h_r), h0 = h + dt*U, g = F/(1+F) from a table
+ * computed in FP64 (rounded once to float for FP32 contexts); FP64 results
+ * are within a few units in the last place of the closed form.
  * Updates the bound elevations in place.  Requires lem_accumulate. */
 LEM_API int lem_erode(lem_ctx* ctx);
 
@@ -214,7 +216,7 @@ LEM_API int lem_trace_read(lem_ctx* ctx, int64_t* ns, int32_t* tags, int cap, in
  * caller's device array dev_h (nx*ny doubles, updated in place) on `stream`
  * (a cudaStream_t, NULL = legacy default), then synchronises that stream and
  * returns the kernel's status.  No context is created and nothing is
- * allocated or freed: the working memory is one fixed array of about 10 MiB
+ * allocated or freed: the working memory is one fixed array of about 20 MiB
  * in the library's device image, held by every GPU that loads the library
  * until the process exits.
  *  - Grids with nx*ny > LEM_NOALLOC_MAX_CELLS (or nx, ny < 3, or invalid

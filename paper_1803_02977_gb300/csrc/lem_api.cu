@@ -32,6 +32,10 @@ struct lem_ctx {
   DevState* st = nullptr;
   int* partial = nullptr;
   int* pq = nullptr;  // block-private queues, pcap entries per block
+  uint8_t* pqm = nullptr;  // donor mask per private-queue entry
+  uint8_t* pqk = nullptr;  // receiver code per private-queue entry
+  int* pqf = nullptr;      // first-donor position per private-queue entry
+  void* cntq = nullptr;    // counts in private-queue order
   int pcap = 0;
   int mode = 0;       // 0: block-private levels with fallback, 1: device-wide only
   int grid = 0;
@@ -57,8 +61,8 @@ int cuda_status(cudaError_t e) {
   } while (0)
 
 // Erosion factors by cell count: F = K*dt*(count*area_scale)^m / d with the
-// same operation order as the per-cell expression, its correctly rounded
-// reciprocal 1/(1+F), and g = F/(1+F) rounded once to float.
+// same operation order as the per-cell expression, g = F/(1+F) by FP64
+// division, and g rounded once to float.
 __global__ void build_tables_kernel(double2* Ftab, float* gtab, double Kdt, double m, double dx,
                                     double dxd, double area_scale) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kTableN; i += gridDim.x * blockDim.x) {
@@ -66,8 +70,8 @@ __global__ void build_tables_kernel(double2* Ftab, float* gtab, double Kdt, doub
     const double P = __dmul_rn(Kdt, pow(A, m));
     const double Fc = __ddiv_rn(P, dx);
     const double Fd = __ddiv_rn(P, dxd);
-    Ftab[i] = make_double2(Fc, __drcp_rn(__dadd_rn(1.0, Fc)));
-    Ftab[kTableN + i] = make_double2(Fd, __drcp_rn(__dadd_rn(1.0, Fd)));
+    Ftab[i] = make_double2(Fc, __ddiv_rn(Fc, __dadd_rn(1.0, Fc)));
+    Ftab[kTableN + i] = make_double2(Fd, __ddiv_rn(Fd, __dadd_rn(1.0, Fd)));
     gtab[i] = (float)(Fc / (1.0 + Fc));
     gtab[kTableN + i] = (float)(Fd / (1.0 + Fd));
   }
@@ -186,7 +190,13 @@ StepArgs<HT, CT> make_args(lem_ctx* c, int phases, int nsteps) {
   a.st = c->st;
   a.partial = c->partial;
   a.pq = c->pq;
+  a.pqm = c->pqm;
+  a.pqk = c->pqk;
+  a.pqf = c->pqf;
+  a.cntq = (CT*)c->cntq;
   a.pcap = c->pcap;
+  a.Udt = c->p.U * c->p.dt;
+  a.Udt_f = (float)(c->p.U * c->p.dt);
   a.phases = phases;
   a.nsteps = nsteps;
   a.frozen = c->frozen ? 1 : 0;
@@ -198,7 +208,7 @@ int launch_typed(lem_ctx* c, int phases, int nsteps) {
   StepArgs<HT, CT> a = make_args<HT, CT>(c, phases, nsteps);
   void* args[] = {&a};
   LEM_CUDA(cudaLaunchCooperativeKernel(step_kernel_ptr<HT, CT>(), dim3(c->grid), dim3(kBD), args,
-                                       0, c->stream));
+                                       kDynSmem, c->stream));
   return LEM_OK;
 }
 
@@ -294,7 +304,10 @@ int lem_create_ex(lem_ctx** out, const lem_params* pin) {
   int nsm = 0, per_sm = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(c), kBD, 0);
+    e = cudaFuncSetAttribute(kernel_for(c), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kDynSmem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(c), kBD, kDynSmem);
   if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
   if (e == cudaSuccess) {
     c->grid = nsm * (per_sm < 2 ? per_sm : 2);
@@ -312,6 +325,11 @@ int lem_create_ex(lem_ctx** out, const lem_params* pin) {
   if (e == cudaSuccess) e = cudaMalloc(&c->st, sizeof(DevState));
   if (e == cudaSuccess) e = cudaMalloc(&c->partial, (size_t)c->grid * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->pq, (size_t)c->grid * c->pcap * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->pqm, (size_t)c->grid * c->pcap);
+  if (e == cudaSuccess) e = cudaMalloc(&c->pqk, (size_t)c->grid * c->pcap);
+  if (e == cudaSuccess) e = cudaMalloc(&c->pqf, (size_t)c->grid * c->pcap * sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMalloc(&c->cntq, (size_t)c->grid * c->pcap * (p.count_bits / 8));
   if (e == cudaSuccess) e = cudaMallocHost(&c->host_status, 4 * sizeof(int));
   if (e == cudaSuccess) {
     DevState s;
@@ -345,6 +363,10 @@ void lem_destroy(lem_ctx* c) {
   cudaFree(c->st);
   cudaFree(c->partial);
   cudaFree(c->pq);
+  cudaFree(c->pqm);
+  cudaFree(c->pqk);
+  cudaFree(c->pqf);
+  cudaFree(c->cntq);
   cudaFree(c->trace);
   if (c->host_status) cudaFreeHost(c->host_status);
   delete c;
@@ -454,11 +476,10 @@ int lem_step(lem_ctx* c, int nsteps) {
   if (nsteps == 0) return LEM_OK;
   int rc = launch_step(c, c->mode == 0 ? (kPhRec | kPhPrivate) : kPhAll, nsteps);
   if (rc != LEM_OK) return rc;
-  if (c->frozen) {
-    c->rec_valid = c->lev_valid = c->acc_valid = true;
-  } else {
-    c->rec_valid = c->lev_valid = c->acc_valid = false;
-  }
+  // A frozen graph's codes and masks stay current; the device-wide queue and
+  // counts are current only if the device-wide form ran (mode 1).
+  c->rec_valid = c->frozen;
+  c->lev_valid = c->acc_valid = c->frozen && c->mode == 1;
   return LEM_OK;
 }
 

@@ -81,6 +81,7 @@ enum TraceTag : int {
   kTrPrivAcc = 12 << 16,    // block 0 finished its private accumulation
   kTrPrivEro = 13 << 16,    // block 0 finished its private erosion
   kTrStepEnd = 14 << 16,    // end-of-step barrier passed
+  kTrLocal = 15 << 16,      // block 0 reached the next barrier (low half: which)
 };
 
 // Record a timestamp (block 0, thread 0 only; no-op when tracing is off).
@@ -112,6 +113,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 __device__ __forceinline__ void set_error(DevState* st, int code) { atomicCAS(&st->err, 0, code); }
+
+// Hint the memory system to bring the line holding p into L1.
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 
 // Device-wide barrier for a co-resident (cooperative) grid.  Thread 0 of each
 // block arrives on a counter; the last arrival resets it and advances the

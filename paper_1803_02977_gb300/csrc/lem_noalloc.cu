@@ -43,9 +43,13 @@ constexpr size_t kOffQueue = kOffMask + align256(kMaxCells);
 constexpr size_t kOffLevels = kOffQueue + align256(sizeof(int) * kMaxCells);
 constexpr size_t kOffCnt = kOffLevels + align256(sizeof(int) * (kMaxCells + 2));
 constexpr size_t kOffPq = kOffCnt + align256(sizeof(int) * kMaxCells);
-constexpr size_t kScratchBytes = kOffPq + align256(sizeof(int) * (size_t)kMaxBlocks * kPcap);
+constexpr size_t kOffPqm = kOffPq + align256(sizeof(int) * (size_t)kMaxBlocks * kPcap);
+constexpr size_t kOffPqk = kOffPqm + align256((size_t)kMaxBlocks * kPcap);
+constexpr size_t kOffPqf = kOffPqk + align256((size_t)kMaxBlocks * kPcap);
+constexpr size_t kOffCntq = kOffPqf + align256(sizeof(int) * (size_t)kMaxBlocks * kPcap);
+constexpr size_t kScratchBytes = kOffCntq + align256(sizeof(int) * (size_t)kMaxBlocks * kPcap);
 
-// The shared working memory of every call on a device (about 10 MiB).
+// The shared working memory of every call on a device (about 20 MiB).
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Device address of g_scratch per device, looked up on first use.
@@ -68,8 +72,8 @@ __global__ void noalloc_prepare_kernel(unsigned char* base, double Kdt, double m
     const double P = __dmul_rn(Kdt, pow(A, m));
     const double Fc = __ddiv_rn(P, dx);
     const double Fd = __ddiv_rn(P, dxd);
-    Ftab[i] = make_double2(Fc, __drcp_rn(__dadd_rn(1.0, Fc)));
-    Ftab[kTableN + i] = make_double2(Fd, __drcp_rn(__dadd_rn(1.0, Fd)));
+    Ftab[i] = make_double2(Fc, __ddiv_rn(Fc, __dadd_rn(1.0, Fc)));
+    Ftab[kTableN + i] = make_double2(Fd, __ddiv_rn(Fd, __dadd_rn(1.0, Fd)));
     gtab[i] = (float)(Fc / (1.0 + Fc));
     gtab[kTableN + i] = (float)(Fd / (1.0 + Fd));
   }
@@ -109,8 +113,11 @@ extern "C" LEM_API int lem_step_noalloc(int nx, int ny, double* dev_h, double dx
   int nsm = 0, per_sm = 0;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return status_of(e);
+  e = cudaFuncSetAttribute((const void*)&lem_step_kernel<double, int>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+  if (e != cudaSuccess) return status_of(e);
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, (const void*)&lem_step_kernel<double, int>, kBD, 0);
+      &per_sm, (const void*)&lem_step_kernel<double, int>, kBD, kDynSmem);
   if (e != cudaSuccess) return status_of(e);
   if (per_sm < 1) return LEM_ECUDA;
   int grid = nsm * per_sm;
@@ -140,7 +147,13 @@ extern "C" LEM_API int lem_step_noalloc(int nx, int ny, double* dev_h, double dx
   a.queue = reinterpret_cast<int*>(base + kOffQueue);
   a.levels = reinterpret_cast<int*>(base + kOffLevels);
   a.pq = reinterpret_cast<int*>(base + kOffPq);
+  a.pqm = base + kOffPqm;
+  a.pqk = base + kOffPqk;
+  a.pqf = reinterpret_cast<int*>(base + kOffPqf);
+  a.cntq = reinterpret_cast<int*>(base + kOffCntq);
   a.pcap = kPcap;
+  a.Udt = U * dt;
+  a.Udt_f = (float)(U * dt);
   a.cnt = reinterpret_cast<int*>(base + kOffCnt);
   a.Ftab = reinterpret_cast<const double2*>(base + kOffFtab);
   a.gtab = reinterpret_cast<const float*>(base + kOffGtab);
@@ -151,7 +164,7 @@ extern "C" LEM_API int lem_step_noalloc(int nx, int ny, double* dev_h, double dx
   a.frozen = 0;
   void* args[] = {&a};
   e = cudaLaunchCooperativeKernel((const void*)&lem_step_kernel<double, int>, dim3(grid),
-                                  dim3(kBD), args, 0, s);
+                                  dim3(kBD), args, kDynSmem, s);
   if (e != cudaSuccess) return status_of(e);
 
   // wait for the step and report the kernel's own status word

@@ -36,8 +36,8 @@
 // FP64 on GB300 runs at about 1/70 of the FP32 rate, so the FP64 work per
 // cell is kept small: receivers compare elevations through their bit
 // patterns and evaluate only the two candidate slopes in FP64 (exact, see
-// receiver_code), and erosion divides by a tabulated reciprocal with one
-// FMA correction step instead of a full division.
+// receiver_code), and erosion uses the increment form of the implicit update
+// with a tabulated F/(1+F) instead of a division (see erode_value).
 #pragma once
 
 #include "lem_device.cuh"
@@ -50,6 +50,8 @@ struct StepArgs {
   HT* h;
   const double* Uf;     // optional per-cell uplift rate
   double U, dt;         // scalar uplift rate, time step
+  double Udt;           // U*dt, as Alg 5 forms it
+  float Udt_f;          // U*dt rounded once to float
   double Kdt;           // K*dt
   double m, dx, dxd;    // area exponent, cardinal and diagonal distance
   double area_scale;
@@ -58,9 +60,13 @@ struct StepArgs {
   int* queue;
   int* levels;
   int* pq;              // block-private queues
+  uint8_t* pqm;         // donor mask of each private-queue entry
+  uint8_t* pqk;         // receiver code of each private-queue entry
+  int* pqf;             // position of each private-queue entry's first donor
+  CT* cntq;             // cell count of each private-queue entry (queue order)
   int pcap;             // entries per block in pq
   CT* cnt;
-  const double2* Ftab;  // {F, 1/(1+F)} for counts < kTableN: [0,N) cardinal, [N,2N) diagonal
+  const double2* Ftab;  // {F, F/(1+F)} for counts < kTableN: [0,N) cardinal, [N,2N) diagonal
   const float* gtab;    // F/(1+F) rounded to float, same layout
   DevState* st;
   int* partial;         // one int per block
@@ -73,6 +79,10 @@ constexpr int kBD = 1024;          // threads per block: one block per SM
 constexpr int kWarps = kBD / 32;
 constexpr int kNarrow = kBD;       // a device-wide level this small runs in block 0
 constexpr int kItems = 4;          // items per thread per round in wide loops
+constexpr int kPItems = 8;         // entries per thread per round of a private level
+constexpr int kStage = 16384;      // emitted entries staged in shared memory per round
+// dynamic shared memory of the step kernel: the staging buffer
+constexpr int kDynSmem = kStage * (int)(sizeof(int) + 1);
 constexpr int kMaxPrivLevels = 2048;  // level offsets a private queue may hold
 
 // ---- Alg 1: receivers ----------------------------------------------------------
@@ -171,10 +181,21 @@ __device__ __forceinline__ int receiver_code(const HT* __restrict__ h, int c, in
   if (worst < B::kInf && no_rounding_merge<HT>(mC, rC, bc) &&
       no_rounding_merge<HT>(mD, rD, bc)) {
     if (kC == kSink && kD == kSink) return kSink;
-    const double hc = (double)hcv;
     if (kD == kSink) return kC;
-    const double sD = __dmul_rn(__dsub_rn(hc, (double)v[kD]), kInvSqrt2);
     if (kC == kSink) return kD;
+    if constexpr (sizeof(HT) == 4) {
+      // FP32 elevations: the FP32 slopes are within 4*2^-24 (relative) of the
+      // FP64 ones, so they decide whenever they differ by more than 2^-18;
+      // only near-ties (and tiny slopes) are compared in FP64.
+      const float sCf = __fsub_rn(hcv, v[kC]);
+      const float sDf = __fmul_rn(__fsub_rn(hcv, v[kD]), 0.70710677f);
+      if (fminf(sCf, sDf) > 1e-30f) {
+        if (sCf > __fmul_rn(sDf, 1.000003814697265625f)) return kC;
+        if (sDf > __fmul_rn(sCf, 1.000003814697265625f)) return kD;
+      }
+    }
+    const double hc = (double)hcv;
+    const double sD = __dmul_rn(__dsub_rn(hc, (double)v[kD]), kInvSqrt2);
     const double sC = __dsub_rn(hc, (double)v[kC]);
     // both slopes are positive: compare their bit patterns
     const long long bC = __double_as_longlong(sC), bD = __double_as_longlong(sD);
@@ -211,7 +232,12 @@ __device__ __forceinline__ int donor_mask(const uint8_t* __restrict__ code, int 
 
 template <typename HT, typename CT>
 __device__ __forceinline__ double uplift_dt(const StepArgs<HT, CT>& a, int c) {
-  return a.Uf ? __dmul_rn(a.Uf[c], a.dt) : __dmul_rn(a.U, a.dt);
+  return a.Uf ? __dmul_rn(a.Uf[c], a.dt) : a.Udt;
+}
+
+template <typename HT, typename CT>
+__device__ __forceinline__ float uplift_dt_f(const StepArgs<HT, CT>& a, int c) {
+  return a.Uf ? (float)__dmul_rn(a.Uf[c], a.dt) : a.Udt_f;
 }
 
 // Alg 5 for a cell without receiver: pits are uplifted, the perimeter is not.
@@ -221,35 +247,34 @@ __device__ __forceinline__ void uplift_sink(const StepArgs<HT, CT>& a, int c) {
   if constexpr (sizeof(HT) == 8) {
     a.h[c] = __dadd_rn(a.h[c], uplift_dt(a, c));
   } else {
-    a.h[c] = __fadd_rn(a.h[c], (float)uplift_dt(a, c));
+    a.h[c] = __fadd_rn(a.h[c], uplift_dt_f(a, c));
   }
 }
 
 // The n = 1 implicit update for one cell of level >= 1, given its receiver
 // code k, count, own elevation hcur and the receiver's updated elevation hr.
-// FP64: h = (h0 + F*hr)/(1+F) with h0 = h + dt*U.  The quotient is
-// q0 = num*inv (inv the correctly rounded 1/(1+F) from the table) refined
-// once by the FMA residual correction of Markstein (IBM J. Res. Dev. 34,
-// 1990): r = num - q0*(1+F) exactly, q = q0 + r*inv.
-// FP32: the increment form h0 - g*(h0 - hr), g = F/(1+F) from the table.
+// The closed form h = (h0 + F*hr)/(1+F), h0 = h + dt*U, is evaluated in the
+// algebraically identical increment form h = h0 - g*(h0 - hr) with
+// g = F/(1+F) taken from a table (computed in FP64 by division for every
+// count below kTableN): one subtraction and one fused multiply-add per cell
+// instead of a division, which GB300 runs about seven times slower than an
+// FMA in FP64.  The results differ from the closed form by a few units in the
+// last place.  FP32 elevations use the same form with g rounded once to float.
 template <typename HT, typename CT>
 __device__ __forceinline__ HT erode_value(const StepArgs<HT, CT>& a, int c, int k, CT count,
                                           HT hcur, HT hr) {
   const bool diag = nbr_diag(k);
   if constexpr (sizeof(HT) == 8) {
     const double h0 = __dadd_rn(hcur, uplift_dt(a, c));
+    double g;
     if (count < (CT)kTableN) {
-      const double2 fi = a.Ftab[(diag ? kTableN : 0) + (int)count];
-      const double num = __dadd_rn(h0, __dmul_rn(fi.x, hr));
-      const double den = __dadd_rn(1.0, fi.x);
-      const double q0 = __dmul_rn(num, fi.y);
-      const double r = __fma_rn(-q0, den, num);
-      return __fma_rn(r, fi.y, q0);
+      g = a.Ftab[(diag ? kTableN : 0) + (int)count].y;
+    } else {
+      const double A = __dmul_rn((double)count, a.area_scale);
+      const double F = __ddiv_rn(__dmul_rn(a.Kdt, pow(A, a.m)), diag ? a.dxd : a.dx);
+      g = __ddiv_rn(F, __dadd_rn(1.0, F));
     }
-    const double A = __dmul_rn((double)count, a.area_scale);
-    const double F = __ddiv_rn(__dmul_rn(a.Kdt, pow(A, a.m)), diag ? a.dxd : a.dx);
-    const double num = __dadd_rn(h0, __dmul_rn(F, hr));
-    return __ddiv_rn(num, __dadd_rn(1.0, F));
+    return __fma_rn(-g, __dsub_rn(h0, hr), h0);
   } else {
     float g;
     if (count < (CT)kTableN) {
@@ -259,7 +284,7 @@ __device__ __forceinline__ HT erode_value(const StepArgs<HT, CT>& a, int c, int 
       const double F = a.Kdt * pow(A, a.m) / (diag ? a.dxd : a.dx);
       g = (float)(F / (1.0 + F));
     }
-    const float h0 = __fadd_rn(hcur, (float)uplift_dt(a, c));
+    const float h0 = __fadd_rn(hcur, uplift_dt_f(a, c));
     return __fmaf_rn(-g, __fsub_rn(h0, hr), h0);
   }
 }
@@ -340,8 +365,11 @@ struct Shared {
   int scan[kWarps];
   long long sum[kWarps];
   int wcount[kWarps];
+  int chunk[kPItems * kWarps];  // per (slot, warp) donor totals, then offsets
+  int chunk_total;
   int plev[kMaxPrivLevels + 1];
 };
+static_assert(kPItems * kWarps == 8 * 32, "one warp scans the chunk totals 8 per lane");
 
 // ---- phase: Alg 1 receivers, Alg 2 donor masks, level 0 of Alg 3 ---------------
 // Returns false if a barrier was abandoned.  On return *n0 holds the number
@@ -367,6 +395,13 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
     }
     for (int base = w0; base < w1; base += 32) {
       const int c = base + lane;
+      // the three rows two iterations ahead, into L1 (in-grid addresses only)
+      const int cp = c + 64;
+      if (!a.frozen && cp < w1 && cp > nx && cp + nx < N) {
+        prefetch_l1(a.h + (cp - nx));
+        prefetch_l1(a.h + cp);
+        prefetch_l1(a.h + (cp + nx));
+      }
       int code = kEdge;
       if (c < w1) {
         if (!a.frozen) {
@@ -392,6 +427,7 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
     for (int i = 0; i < kWarps; ++i) tot += s.wcount[i];
     a.partial[b] = tot;
   }
+  trace_point(a.st, kTrLocal + 1);
   if (!grid_barrier(a.st, G)) return false;
   trace_point(a.st, kTrCodes);
 
@@ -405,6 +441,8 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
   // donor masks and the cells without receiver, ascending, into the global
   // level 0 and this block's private level 0
   int* pq = a.pq + (size_t)b * a.pcap;
+  uint8_t* pqm = a.pqm + (size_t)b * a.pcap;
+  uint8_t* pqk = a.pqk + (size_t)b * a.pcap;
   {
     int x = w0 + lane, y = 0;
     if (w0 < w1) {
@@ -414,16 +452,29 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
     int run = wpre;
     for (int base = w0; base < w1; base += 32) {
       const int c = base + lane;
+      const int cp = c + 64;
+      if (cp < w1 && cp > nx && cp + nx < N) {
+        prefetch_l1(a.code + (cp - nx));
+        prefetch_l1(a.code + cp);
+        prefetch_l1(a.code + (cp + nx));
+      }
       bool f = false;
+      int msk = 0, cd = kEdge;
       if (c < w1) {
-        a.mask[c] = (uint8_t)donor_mask(a.code, c, x, y, nx, ny);
-        f = no_receiver(a.code[c]);
+        msk = donor_mask(a.code, c, x, y, nx, ny);
+        a.mask[c] = (uint8_t)msk;
+        cd = a.code[c];
+        f = no_receiver(cd);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, f);
       if (f) {
         const int pos = run + __popc(bal & ((1u << lane) - 1u));
         a.queue[prefix + pos] = c;
-        if (pos < a.pcap) pq[pos] = c;
+        if (pos < a.pcap) {
+          pq[pos] = c;
+          pqm[pos] = (uint8_t)msk;
+          pqk[pos] = (uint8_t)cd;
+        }
       }
       run += __popc(bal);
       x += 32;
@@ -437,6 +488,8 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
     a.levels[0] = 0;
     a.levels[1] = total;
   }
+  __syncthreads();
+  trace_point(a.st, kTrLocal + 2);
   if (!grid_barrier(a.st, G)) return false;
   trace_point(a.st, kTrLevel0);
   return true;
@@ -661,7 +714,15 @@ __device__ __noinline__ int phase_private(const StepArgs<HT, CT>& a, Shared& s, 
   const int b = blockIdx.x, t = threadIdx.x;
   const int nx = a.nx;
   int* pq = a.pq + (size_t)b * a.pcap;
-  // Alg 3 on this block's trees
+  uint8_t* pqm = a.pqm + (size_t)b * a.pcap;
+  uint8_t* pqk = a.pqk + (size_t)b * a.pcap;
+  int* pqf = a.pqf + (size_t)b * a.pcap;
+  extern __shared__ unsigned char dyn_smem[];
+  int* stage_q = reinterpret_cast<int*>(dyn_smem);
+  uint8_t* stage_k = dyn_smem + sizeof(int) * kStage;
+  // Alg 3 on this block's trees.  Each entry carries its donor mask and its
+  // receiver code, written when it is emitted, so later levels and sweeps
+  // read them in queue order instead of gathering them.
   bool ovf = n0 > a.pcap;
   int lo = 0, hi = n0, PL = 1;
   if (t == 0) {
@@ -670,33 +731,113 @@ __device__ __noinline__ int phase_private(const StepArgs<HT, CT>& a, Shared& s, 
   }
   while (!ovf && lo < hi) {
     int run = hi;
-    for (int base0 = lo; base0 < hi; base0 += kItems * kBD) {
-      const int base = base0 + kItems * t;
-      int cs[kItems], ms[kItems];
+    // Order within a private level is free (its cells are independent), so
+    // thread t takes the strided entries base + i*kBD + t, i < kPItems: the
+    // entry loads coalesce and all kPItems mask gathers are in flight at once.
+    for (int base = lo; base < hi; base += kPItems * kBD) {
+      int cs[kPItems], ms[kPItems];
 #pragma unroll
-      for (int i = 0; i < kItems; ++i) cs[i] = (base + i < hi) ? pq[base + i] : -1;
-      int mine = 0;
-#pragma unroll
-      for (int i = 0; i < kItems; ++i) {
-        ms[i] = (cs[i] >= 0) ? a.mask[cs[i]] : 0;
-        mine += __popc(ms[i]);
+      for (int i = 0; i < kPItems; ++i) {
+        const int j = base + i * kBD + t;
+        cs[i] = (j < hi) ? pq[j] : -1;
       }
-      int tot;
-      int pos = run + block_exclusive_scan<kBD>(mine, &tot, s.scan);
+      if (lo == 0) {
+#pragma unroll
+        for (int i = 0; i < kPItems; ++i) ms[i] = (cs[i] >= 0) ? pqm[base + i * kBD + t] : 0;
+      } else {
+        // gather this level's masks and keep them beside the entries for the
+        // accumulation sweep
+#pragma unroll
+        for (int i = 0; i < kPItems; ++i) ms[i] = (cs[i] >= 0) ? a.mask[cs[i]] : 0;
+#pragma unroll
+        for (int i = 0; i < kPItems; ++i)
+          if (cs[i] >= 0) pqm[base + i * kBD + t] = (uint8_t)ms[i];
+      }
+      // Output offsets in parent order: entry base + i*kBD + t is the
+      // (i*kBD + t)-th parent of the round, so the next level keeps this
+      // level's order and donors of neighbouring cells stay neighbours.
+      // Each warp scans its 32 lanes per slot i; warp 0 then scans the
+      // kPItems*kWarps (slot, warp) chunk totals.
+      const int lane = t & 31, w = t >> 5;
+      int pos_i[kPItems];
+#pragma unroll
+      for (int i = 0; i < kPItems; ++i) {
+        const int cnt = __popc(ms[i]);
+        int x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        pos_i[i] = x - cnt;
+        if (lane == 31) s.chunk[i * kWarps + w] = x;
+      }
+      __syncthreads();
+      if (w == 0) {
+        int v[8], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          v[q] = s.chunk[lane * 8 + q];
+          sum += v[q];
+        }
+        int x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (lane == 31) s.chunk_total = x;
+        int acc = x - sum;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          s.chunk[lane * 8 + q] = acc;
+          acc += v[q];
+        }
+      }
+      __syncthreads();
+      const int tot = s.chunk_total;
+#pragma unroll
+      for (int i = 0; i < kPItems; ++i) pos_i[i] += run + s.chunk[i * kWarps + w];
+      __syncthreads();  // chunk[] is rewritten by the next round
       if (run + tot > a.pcap) {
         ovf = true;
         break;
       }
+      // each entry's donors are emitted contiguously; remember where they
+      // start.  The emitted entries are staged in shared memory so that the
+      // queue is written with coalesced stores.
+      const bool staged = tot <= kStage;
 #pragma unroll
-      for (int i = 0; i < kItems; ++i) {
-        if (ms[i]) {
-          emit_donors(pq, pos, cs[i], ms[i], nx);
-          pos += __popc(ms[i]);
+      for (int i = 0; i < kPItems; ++i) {
+        int pos = pos_i[i];
+        if (cs[i] >= 0) pqf[base + i * kBD + t] = pos;
+        int msk = ms[i];
+        while (msk) {
+          const int k = __ffs(msk) - 1;
+          msk &= msk - 1;
+          const int d = cs[i] + nbr_off(k, nx);
+          if (staged) {
+            stage_q[pos - run] = d;
+            stage_k[pos - run] = (uint8_t)(7 - k);
+          } else {
+            pq[pos] = d;
+            pqk[pos] = (uint8_t)(7 - k);
+          }
+          ++pos;
         }
+      }
+      if (staged) {
+        __syncthreads();
+        for (int o = t; o < tot; o += kBD) {
+          pq[run + o] = stage_q[o];
+          pqk[run + o] = stage_k[o];
+        }
+        __syncthreads();
       }
       run += tot;
     }
     __syncthreads();
+    trace_point(a.st, kTrLocal + 0x1000 + PL);  // block 0: private level PL-1 expanded
     if (ovf || run == hi) break;
     if (PL >= kMaxPrivLevels) {
       ovf = true;
@@ -708,38 +849,76 @@ __device__ __noinline__ int phase_private(const StepArgs<HT, CT>& a, Shared& s, 
     hi = run;
   }
   if (ovf && t == 0) a.st->private_overflow = 1;
+  trace_point(a.st, kTrLocal + 3);
   if (!grid_barrier(a.st, G)) return -1;
   trace_point(a.st, kTrPrivBfs);
   if (ld_volatile(&a.st->private_overflow)) return 0;
 
-  // Alg 4, this block's levels from the highest down
-  for (int l = PL - 1; l >= 0; --l) {
+  // Alg 4 in queue order, this block's levels from the highest down to level
+  // 1 (a time step needs the counts of eroding cells only): an entry's count
+  // is 1 plus the counts of its donors, which sit contiguously at
+  // [pqf, pqf + number of donors) in the next level.
+  CT* cntq = a.cntq + (size_t)b * a.pcap;
+  for (int l = PL - 1; l >= 1; --l) {
     const int l0 = s.plev[l], l1 = s.plev[l + 1];
     for (int base = l0 + t; base < l1; base += kItems * kBD) {
-      int cs[kItems];
+      int fs[kItems], ns[kItems];
 #pragma unroll
       for (int i = 0; i < kItems; ++i) {
         const int j = base + i * kBD;
-        cs[i] = (j < l1) ? pq[j] : -1;
+        fs[i] = (j < l1) ? pqf[j] : 0;
+        ns[i] = (j < l1) ? __popc(pqm[j]) : 0;
       }
-      accumulate_items(a, cs);
+      CT sum[kItems];
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        sum[i] = 1;
+        for (int q = 0; q < ns[i]; ++q) sum[i] += cntq[fs[i] + q];
+      }
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        const int j = base + i * kBD;
+        if (j < l1) cntq[j] = sum[i];
+      }
     }
     __syncthreads();
+    trace_point(a.st, kTrLocal + 0x2000 + l);  // block 0: private level l accumulated
   }
   trace_point(a.st, kTrPrivAcc);
-  // Alg 5 on level 0, then Alg 6 from level 1 up
-  for (int j = t; j < s.plev[1]; j += kBD) uplift_sink(a, pq[j]);
+  // Alg 5 on level 0 (pits only), then Alg 6 from level 1 up
+  for (int j = t; j < s.plev[1]; j += kBD)
+    if (pqk[j] == kSink) {
+      const int c = pq[j];
+      if constexpr (sizeof(HT) == 8) {
+        a.h[c] = __dadd_rn(a.h[c], uplift_dt(a, c));
+      } else {
+        a.h[c] = __fadd_rn(a.h[c], uplift_dt_f(a, c));
+      }
+    }
   __syncthreads();
   for (int l = 1; l < PL; ++l) {
     const int l0 = s.plev[l], l1 = s.plev[l + 1];
     for (int base = l0 + t; base < l1; base += kItems * kBD) {
-      int cs[kItems];
+      int cs[kItems], ks[kItems];
+      CT ns[kItems];
+      HT hc[kItems], hr[kItems];
 #pragma unroll
       for (int i = 0; i < kItems; ++i) {
         const int j = base + i * kBD;
         cs[i] = (j < l1) ? pq[j] : -1;
+        ks[i] = (j < l1) ? pqk[j] : 0;
+        ns[i] = (j < l1) ? cntq[j] : 1;
       }
-      erode_items(a, cs);
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        if (cs[i] >= 0) {
+          hc[i] = a.h[cs[i]];
+          hr[i] = a.h[cs[i] + nbr_off(ks[i], nx)];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kItems; ++i)
+        if (cs[i] >= 0) a.h[cs[i]] = erode_value(a, cs[i], ks[i], ns[i], hc[i], hr[i]);
     }
     __syncthreads();
   }

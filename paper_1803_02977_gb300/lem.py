@@ -66,7 +66,7 @@ LEM_NOALLOC_MAX_CELLS = 1 << 18
 TRACE_PHASES = {1: "start", 2: "receivers", 3: "level0", 4: "bfs_wide", 5: "bfs_narrow",
                 6: "acc_wide", 7: "acc_narrow", 8: "uplift", 9: "erode_wide",
                 10: "erode_narrow", 11: "private_levels", 12: "private_accumulate",
-                13: "private_erode", 14: "step_end"}
+                13: "private_erode", 14: "step_end", 15: "block0_done"}
 
 
 def lib(build_if_missing: bool = True):
