@@ -202,6 +202,75 @@ LEM_API int lem_trace_enable(lem_ctx* ctx, int capacity);
  * 10 narrow erosion. */
 LEM_API int lem_trace_read(lem_ctx* ctx, int64_t* ns, int32_t* tags, int cap, int* n);
 
+/* Reverse-mode gradient of nsteps time steps (Alg 5 + Alg 6, n-hat = 1)
+ * started from dev_h0, for the inverse problems the paper's introduction
+ * motivates; the paper itself has no adjoint.  Each step's receiver graph is
+ * frozen (its derivative is zero almost everywhere).  With mu the adjoint of
+ * a step's output, swept donors first, mu_c = lambda_c + sum over donors d of
+ * mu_d F_d/(1+F_d); then dL/dh_c = mu_c/(1+F_c), dL/dU_c += dt mu_c/(1+F_c)
+ * and dL/dK += mu_c (h'_r - h'_c)/(1+F_c) dt A_c^m/d_c for eroding cells
+ * (pits: mu_c and dt mu_c; perimeter: mu_c).
+ *  dev_h0        nx*ny doubles, the run's initial elevations (not modified)
+ *  dev_lambda_T  nx*ny doubles, dL/dh after the last step
+ *  nsteps        number of steps (>= 1); the context's parameters and uplift
+ *                field (lem_set_uplift_field) define them
+ *  ckpt_every    the forward is recomputed from a checkpoint kept every
+ *                ckpt_every steps; at most ckpt_every+1 states are stored
+ *  dev_dLdU      nx*ny doubles receiving dL/dU per cell (zero on the
+ *                perimeter)
+ *  dLdK          host double receiving dL/dK
+ *  dev_lambda_0  optional nx*ny doubles receiving dL/dh0
+ * FP64 contexts with 32-bit counts only.  Allocates and frees its
+ * checkpoint and segment buffers; synchronises the stream.  The context's
+ * elevation binding is restored on return. */
+LEM_API int lem_adjoint(lem_ctx* ctx, const double* dev_h0, const double* dev_lambda_T,
+                        int nsteps, int ckpt_every, double* dev_dLdU, double* dLdK,
+                        double* dev_lambda_0);
+
+/* ---- Many realizations in one launch ------------------------------------
+ * The paper motivates its algorithm by the many model realizations that
+ * inverse problems and statistical studies need (abstract; Section
+ * "Introduction"), and notes that a GPU's spare capacity can process other
+ * models simultaneously (Section "GPU Implementation").  A batch holds R
+ * independent grids of any sizes and parameters, FP32 elevations packed
+ * back to back (realization r at offsets[r] .. offsets[r+1]), and advances
+ * all of them in one launch: each thread block claims the largest grid not
+ * yet taken and runs its time steps alone with block barriers.  Receivers
+ * use FP64 slope tests as in lem_receivers; erosion uses the FP32 increment
+ * form with 32-bit cell counts and area = dx*dx. */
+typedef struct lem_batch lem_batch;
+
+/* Create a batch of R grids; nx, ny, dx, K, m, U, dt are host arrays of R
+ * entries (same meaning and limits as lem_params).  dtype must be LEM_F32.
+ * Allocates about 20 bytes of device scratch per cell. */
+LEM_API int lem_batch_create(lem_batch** out, int R, const int* nx, const int* ny,
+                             const double* dx, const double* K, const double* m,
+                             const double* U, const double* dt, int dtype);
+
+/* Free the batch.  NULL is ignored. */
+LEM_API void lem_batch_destroy(lem_batch* batch);
+
+/* Host array of R+1 cell offsets of the packed layout (offsets[R] = total). */
+LEM_API int lem_batch_offsets(const lem_batch* batch, int64_t* offsets);
+
+/* Issue later work on `stream` (a cudaStream_t; NULL = legacy default). */
+LEM_API int lem_batch_set_stream(lem_batch* batch, void* stream);
+
+/* Bind the caller's packed FP32 elevations (offsets[R] floats), updated in
+ * place by lem_batch_step. */
+LEM_API int lem_batch_bind_elevation(lem_batch* batch, float* dev_h);
+
+/* Kernel shape: threads per block (256, 512 or 1024) and breadth-first
+ * entries per thread per round (4 or 8).  Default 1024 x 4.  The package's
+ * autotuner picks it by timing; any shape gives the same results. */
+LEM_API int lem_batch_set_config(lem_batch* batch, int block_threads, int items_per_thread);
+
+/* Advance every realization by nsteps time steps (asynchronous). */
+LEM_API int lem_batch_step(lem_batch* batch, int nsteps);
+
+/* Synchronise the batch's stream; returns LEM_ECUDA if a kernel failed. */
+LEM_API int lem_batch_sync(lem_batch* batch);
+
 /* Largest grid (nx*ny cells) accepted by lem_step_noalloc. */
 #define LEM_NOALLOC_MAX_CELLS (1 << 18)
 

@@ -11,40 +11,12 @@
 #include <vector>
 
 #include "lem.h"
+#include "lem_context.cuh"
 #include "lem_step_kernel.cuh"
 
 using namespace lem;
 
-struct lem_ctx {
-  lem_params p;
-  int N = 0;
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  void* h = nullptr;
-  const double* Uf = nullptr;
-  uint8_t* code = nullptr;
-  uint8_t* mask = nullptr;
-  int* queue = nullptr;
-  int* levels = nullptr;
-  void* cnt = nullptr;
-  double2* Ftab = nullptr;
-  float* gtab = nullptr;
-  DevState* st = nullptr;
-  int* partial = nullptr;
-  int* pq = nullptr;  // block-private queues, pcap entries per block
-  uint8_t* pqm = nullptr;  // donor mask per private-queue entry
-  uint8_t* pqk = nullptr;  // receiver code per private-queue entry
-  int* pqf = nullptr;      // first-donor position per private-queue entry
-  void* cntq = nullptr;    // counts in private-queue order
-  int pcap = 0;
-  int mode = 0;       // 0: block-private levels with fallback, 1: device-wide only
-  int grid = 0;
-  int* host_status = nullptr;  // pinned: [err, nlevels]
-  bool rec_valid = false, lev_valid = false, acc_valid = false, frozen = false;
-  double Kdt = 0, dxd = 0, area_scale = 0;
-  double wait_limit_s = 2.0;
-  unsigned long long* trace = nullptr;  // device trace buffer (lem_trace_enable)
-};
+
 
 namespace {
 
@@ -62,12 +34,16 @@ int cuda_status(cudaError_t e) {
 
 // Erosion factors by cell count: F = K*dt*(count*area_scale)^m / d with the
 // same operation order as the per-cell expression, g = F/(1+F) by FP64
-// division, and g rounded once to float.
-__global__ void build_tables_kernel(double2* Ftab, float* gtab, double Kdt, double m, double dx,
-                                    double dxd, double area_scale) {
+// division, g rounded once to float, and dF/dK = dt*A^m/d for the adjoint.
+__global__ void build_tables_kernel(double2* Ftab, float* gtab, double2* Gtab, double Kdt,
+                                    double dt, double m, double dx, double dxd,
+                                    double area_scale) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kTableN; i += gridDim.x * blockDim.x) {
     const double A = __dmul_rn((double)i, area_scale);
-    const double P = __dmul_rn(Kdt, pow(A, m));
+    const double Am = pow(A, m);
+    const double Gp = __dmul_rn(dt, Am);
+    Gtab[i] = make_double2(__ddiv_rn(Gp, dx), __ddiv_rn(Gp, dxd));
+    const double P = __dmul_rn(Kdt, Am);
     const double Fc = __ddiv_rn(P, dx);
     const double Fd = __ddiv_rn(P, dxd);
     Ftab[i] = make_double2(Fc, __ddiv_rn(Fc, __dadd_rn(1.0, Fc)));
@@ -322,6 +298,7 @@ int lem_create_ex(lem_ctx** out, const lem_params* pin) {
   if (e == cudaSuccess) e = cudaMalloc(&c->cnt, N * (p.count_bits / 8));
   if (e == cudaSuccess) e = cudaMalloc(&c->Ftab, 2 * kTableN * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc(&c->gtab, 2 * kTableN * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&c->Gtab, kTableN * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc(&c->st, sizeof(DevState));
   if (e == cudaSuccess) e = cudaMalloc(&c->partial, (size_t)c->grid * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->pq, (size_t)c->grid * c->pcap * sizeof(int));
@@ -338,7 +315,8 @@ int lem_create_ex(lem_ctx** out, const lem_params* pin) {
     e = cudaMemcpy(c->st, &s, sizeof(s), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) {
-    build_tables_kernel<<<64, 256>>>(c->Ftab, c->gtab, c->Kdt, p.m, p.dx, c->dxd, c->area_scale);
+    build_tables_kernel<<<64, 256>>>(c->Ftab, c->gtab, c->Gtab, c->Kdt, p.dt, p.m, p.dx, c->dxd,
+                                     c->area_scale);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -360,6 +338,7 @@ void lem_destroy(lem_ctx* c) {
   cudaFree(c->cnt);
   cudaFree(c->Ftab);
   cudaFree(c->gtab);
+  cudaFree(c->Gtab);
   cudaFree(c->st);
   cudaFree(c->partial);
   cudaFree(c->pq);

@@ -1,0 +1,40 @@
+// lem_context.cuh -- the context behind the opaque lem_ctx handle of
+// include/lem.h: parameters, the caller's bound buffers and the library's own
+// device scratch.  Shared by the C-ABI translation units.
+#pragma once
+
+#include "lem.h"
+#include "lem_step_kernel.cuh"
+
+struct lem_ctx {
+  // parameters and bound caller buffers
+  lem_params p;
+  int N = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  void* h = nullptr;
+  const double* Uf = nullptr;
+  uint8_t* code = nullptr;
+  uint8_t* mask = nullptr;
+  int* queue = nullptr;
+  int* levels = nullptr;
+  void* cnt = nullptr;
+  double2* Ftab = nullptr;  // {F, F/(1+F)} by count (lem_step_kernel.cuh)
+  double2* Gtab = nullptr;  // {dt*A^m/dx, dt*A^m/(dx*sqrt2)} = dF/dK by count
+  float* gtab = nullptr;
+  lem::DevState* st = nullptr;
+  int* partial = nullptr;
+  int* pq = nullptr;  // block-private queues, pcap entries per block
+  uint8_t* pqm = nullptr;  // donor mask per private-queue entry
+  uint8_t* pqk = nullptr;  // receiver code per private-queue entry
+  int* pqf = nullptr;      // first-donor position per private-queue entry
+  void* cntq = nullptr;    // counts in private-queue order
+  int pcap = 0;
+  int mode = 0;       // 0: block-private levels with fallback, 1: device-wide only
+  int grid = 0;
+  int* host_status = nullptr;  // pinned: [err, nlevels]
+  bool rec_valid = false, lev_valid = false, acc_valid = false, frozen = false;
+  double Kdt = 0, dxd = 0, area_scale = 0;
+  double wait_limit_s = 2.0;
+  unsigned long long* trace = nullptr;  // device trace buffer (lem_trace_enable)
+};

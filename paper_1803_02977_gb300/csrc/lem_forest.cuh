@@ -1,0 +1,271 @@
+// lem_forest.cuh -- one thread block runs Algs 1-6 of Barnes (arXiv:1803.02977)
+// on a whole grid by itself, with block barriers only.  Used by the batched
+// form, where each block owns one realization at a time.
+//
+// The queue of a grid lives in global memory in breadth-first order: level 0
+// (cells without receiver) first, then each level's donors in the order of
+// their receivers, each entry with its donor mask (pqm), receiver code (pqk)
+// and the position of its first donor (pqf).  Accumulation then runs in
+// queue order on a queue-ordered count array; erosion gathers elevations.
+#pragma once
+
+#include "lem_step_kernel.cuh"
+
+namespace lem {
+
+template <int BD, int PI>
+struct ForestSmem {
+  static constexpr int kW = BD / 32;
+  int chunk[PI * kW];
+  int chunk_total;
+  int wcount[kW];
+  int wbase[kW];
+};
+
+struct ForestGrid {
+  int nx, ny, N;
+  float* h;
+  uint8_t* code;
+  uint8_t* mask;
+  int* pq;
+  uint8_t* pqm;
+  uint8_t* pqk;
+  int* pqf;
+  int* cntq;
+  int* plev;       // level offsets, capacity N + 1
+  float Udt;       // U*dt, rounded once to float
+};
+
+// Algs 1-2 and level 0 of Alg 3 over the whole grid: receiver codes, donor
+// masks, and the cells without receiver (ascending) as queue level 0.
+// Returns n0.  Each warp owns one contiguous range of cells.
+template <int BD, int PI>
+__device__ int forest_receivers(const ForestGrid& g, ForestSmem<BD, PI>& s) {
+  constexpr int W = BD / 32;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int nx = g.nx, ny = g.ny, N = g.N;
+  const int wchunk = ((N + W - 1) / W + 31) & ~31;
+  const int w0 = min(N, w * wchunk), w1 = min(N, w0 + wchunk);
+  int wcnt = 0;
+  {
+    int x = w0 + lane, y = x / nx;
+    x -= y * nx;
+    for (int base = w0; base < w1; base += 32) {
+      const int c = base + lane;
+      int cd = kEdge;
+      if (c < w1) {
+        const bool perim = (x == 0 || y == 0 || x == nx - 1 || y == ny - 1);
+        cd = perim ? kEdge : receiver_code(g.h, c, nx);
+        g.code[c] = (uint8_t)cd;
+      }
+      wcnt += __popc(__ballot_sync(0xffffffffu, c < w1 && no_receiver(cd)));
+      x += 32;
+      while (x >= nx) {
+        x -= nx;
+        ++y;
+      }
+    }
+  }
+  if (lane == 0) s.wcount[w] = wcnt;
+  __syncthreads();
+  if (t == 0) {
+    int acc = 0;
+    for (int i = 0; i < W; ++i) {
+      s.wbase[i] = acc;
+      acc += s.wcount[i];
+    }
+    s.chunk_total = acc;
+  }
+  __syncthreads();
+  const int n0 = s.chunk_total;
+  {
+    int x = w0 + lane, y = x / nx;
+    x -= y * nx;
+    int run = s.wbase[w];
+    for (int base = w0; base < w1; base += 32) {
+      const int c = base + lane;
+      bool f = false;
+      int msk = 0, cd = kEdge;
+      if (c < w1) {
+        msk = donor_mask(g.code, c, x, y, nx, ny);
+        g.mask[c] = (uint8_t)msk;
+        cd = g.code[c];
+        f = no_receiver(cd);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (f) {
+        const int pos = run + __popc(bal & ((1u << lane) - 1u));
+        g.pq[pos] = c;
+        g.pqm[pos] = (uint8_t)msk;
+        g.pqk[pos] = (uint8_t)cd;
+      }
+      run += __popc(bal);
+      x += 32;
+      while (x >= nx) {
+        x -= nx;
+        ++y;
+      }
+    }
+  }
+  __syncthreads();
+  return n0;
+}
+
+// Alg 3: expand levels from level 0 = [0, n0).  Entries of a round are taken
+// PI per thread (strided, so the loads coalesce) and emitted in parent order.
+// Returns the number of levels PL; plev[0..PL] holds the offsets.
+template <int BD, int PI>
+__device__ int forest_levels(const ForestGrid& g, int n0, ForestSmem<BD, PI>& s) {
+  constexpr int W = BD / 32;
+  constexpr int C = PI * W;          // chunk totals per round
+  constexpr int PER = (C + 31) / 32;  // chunk totals per lane of warp 0
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int nx = g.nx;
+  int lo = 0, hi = n0, PL = 1;
+  if (t == 0) {
+    g.plev[0] = 0;
+    g.plev[1] = n0;
+  }
+  while (lo < hi) {
+    int run = hi;
+    for (int base = lo; base < hi; base += PI * BD) {
+      int cs[PI], ms[PI];
+#pragma unroll
+      for (int i = 0; i < PI; ++i) {
+        const int j = base + i * BD + t;
+        cs[i] = (j < hi) ? g.pq[j] : -1;
+      }
+      if (lo == 0) {
+#pragma unroll
+        for (int i = 0; i < PI; ++i) ms[i] = (cs[i] >= 0) ? g.pqm[base + i * BD + t] : 0;
+      } else {
+#pragma unroll
+        for (int i = 0; i < PI; ++i) ms[i] = (cs[i] >= 0) ? g.mask[cs[i]] : 0;
+#pragma unroll
+        for (int i = 0; i < PI; ++i)
+          if (cs[i] >= 0) g.pqm[base + i * BD + t] = (uint8_t)ms[i];
+      }
+      int pos_i[PI];
+#pragma unroll
+      for (int i = 0; i < PI; ++i) {
+        const int cnt = __popc(ms[i]);
+        int x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        pos_i[i] = x - cnt;
+        if (lane == 31) s.chunk[i * W + w] = x;
+      }
+      __syncthreads();
+      if (w == 0) {
+        int v[PER], sum = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          const int idx = lane * PER + q;
+          v[q] = (idx < C) ? s.chunk[idx] : 0;
+          sum += v[q];
+        }
+        int x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (lane == 31) s.chunk_total = x;
+        int acc = x - sum;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          const int idx = lane * PER + q;
+          if (idx < C) s.chunk[idx] = acc;
+          acc += v[q];
+        }
+      }
+      __syncthreads();
+      const int tot = s.chunk_total;
+#pragma unroll
+      for (int i = 0; i < PI; ++i) pos_i[i] += run + s.chunk[i * W + w];
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < PI; ++i) {
+        int pos = pos_i[i];
+        if (cs[i] >= 0) g.pqf[base + i * BD + t] = pos;
+        int msk = ms[i];
+        while (msk) {
+          const int k = __ffs(msk) - 1;
+          msk &= msk - 1;
+          g.pq[pos] = cs[i] + nbr_off(k, nx);
+          g.pqk[pos] = (uint8_t)(7 - k);
+          ++pos;
+        }
+      }
+      run += tot;
+    }
+    __syncthreads();
+    if (run == hi) break;
+    ++PL;
+    if (t == 0) g.plev[PL] = run;
+    lo = hi;
+    hi = run;
+  }
+  __syncthreads();
+  return PL;
+}
+
+// Alg 4 in queue order, levels PL-1 down to 1: 1 + the counts of the donors
+// at [pqf, pqf + popc(pqm)).
+template <int BD>
+__device__ void forest_accumulate(const ForestGrid& g, int PL) {
+  const int t = threadIdx.x;
+  for (int l = PL - 1; l >= 1; --l) {
+    const int l0 = g.plev[l], l1 = g.plev[l + 1];
+    for (int j = l0 + t; j < l1; j += BD) {
+      const int f = g.pqf[j], n = __popc(g.pqm[j]);
+      int sum = 1;
+      for (int q = 0; q < n; ++q) sum += g.cntq[f + q];
+      g.cntq[j] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+// g = F/(1+F) for this grid's parameters; small counts come from a
+// shared-memory table built per realization.
+struct ErosionFactors {
+  const float* tab;  // [0,TN) cardinal, [TN,2TN) diagonal
+  int TN;
+  double Kdt, m, dx, dxd, area;
+  __device__ float operator()(int count, bool diag) const {
+    if (count < TN) return tab[(diag ? TN : 0) + count];
+    const double A = (double)count * area;
+    const double F = Kdt * pow(A, m) / (diag ? dxd : dx);
+    return (float)(F / (1.0 + F));
+  }
+};
+
+// Algs 5-6 (FP32 increment form): uplift level-0 pits, then levels 1 up.
+template <int BD>
+__device__ void forest_erode(const ForestGrid& g, int PL, const ErosionFactors& ef) {
+  const int t = threadIdx.x;
+  const int n0 = g.plev[1];
+  for (int j = t; j < n0; j += BD)
+    if (g.pqk[j] == kSink) {
+      const int c = g.pq[j];
+      g.h[c] = __fadd_rn(g.h[c], g.Udt);
+    }
+  __syncthreads();
+  for (int l = 1; l < PL; ++l) {
+    const int l0 = g.plev[l], l1 = g.plev[l + 1];
+    for (int j = l0 + t; j < l1; j += BD) {
+      const int c = g.pq[j], k = g.pqk[j];
+      const float gk = ef(g.cntq[j], nbr_diag(k));
+      const float h0 = __fadd_rn(g.h[c], g.Udt);
+      const float hr = g.h[c + nbr_off(k, g.nx)];
+      g.h[c] = __fmaf_rn(-gk, __fsub_rn(h0, hr), h0);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace lem

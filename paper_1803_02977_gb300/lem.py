@@ -57,6 +57,15 @@ SIGNATURES = [
     ("lem_step_stats", _I, [_VP, _I64P, _I64P]),
     ("lem_trace_enable", _I, [_VP, _I]),
     ("lem_trace_read", _I, [_VP, _VP, _VP, _I, ctypes.POINTER(_I)]),
+    ("lem_adjoint", _I, [_VP, _VP, _VP, _I, _I, _VP, ctypes.POINTER(_D), _VP]),
+    ("lem_batch_create", _I, [ctypes.POINTER(_VP), _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I]),
+    ("lem_batch_destroy", None, [_VP]),
+    ("lem_batch_offsets", _I, [_VP, _VP]),
+    ("lem_batch_set_stream", _I, [_VP, _VP]),
+    ("lem_batch_bind_elevation", _I, [_VP, _VP]),
+    ("lem_batch_set_config", _I, [_VP, _I, _I]),
+    ("lem_batch_step", _I, [_VP, _I]),
+    ("lem_batch_sync", _I, [_VP]),
     ("lem_step_noalloc", _I, [_I, _I, _VP, _D, _D, _D, _D, _D, _I, _VP]),
     ("lem_status_string", ctypes.c_char_p, [_I]),
 ]
@@ -187,6 +196,109 @@ def lem_step_stats(ctx):
     p, g = ctypes.c_int64(0), ctypes.c_int64(0)
     _check(lib().lem_step_stats(ctx, ctypes.byref(p), ctypes.byref(g)), "lem_step_stats")
     return p.value, g.value
+
+
+def lem_adjoint(ctx, h0, lambda_T, nsteps, ckpt_every, dLdU, lambda_0=None):
+    """Fills dLdU (and lambda_0 if given); returns dL/dK."""
+    k = ctypes.c_double(0.0)
+    _check(lib().lem_adjoint(ctx, _ptr(h0), _ptr(lambda_T), nsteps, ckpt_every, _ptr(dLdU),
+                             ctypes.byref(k), _ptr(lambda_0)), "lem_adjoint")
+    return k.value
+
+
+def _host(arr, ctype):
+    import numpy as np
+    a = np.ascontiguousarray(arr, dtype=ctype)
+    return a, a.ctypes.data_as(_VP)
+
+
+def lem_batch_create(nx, ny, dx, K, m, U, dt, dtype=LEM_F32):
+    import numpy as np
+    R = len(nx)
+    keep = [_host(nx, np.int32), _host(ny, np.int32)] + [_host(v, np.float64)
+                                                        for v in (dx, K, m, U, dt)]
+    b = _VP()
+    _check(lib().lem_batch_create(ctypes.byref(b), R, *[p for _, p in keep], dtype),
+           "lem_batch_create")
+    return b
+
+
+def lem_batch_destroy(b):
+    lib().lem_batch_destroy(b)
+
+
+def lem_batch_offsets(b, R):
+    import numpy as np
+    off = np.zeros(R + 1, np.int64)
+    _check(lib().lem_batch_offsets(b, off.ctypes.data_as(_VP)), "lem_batch_offsets")
+    return off
+
+
+def lem_batch_set_stream(b, stream=None):
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(lib().lem_batch_set_stream(b, ctypes.c_void_p(s)), "lem_batch_set_stream")
+
+
+def lem_batch_bind_elevation(b, h):
+    _check(lib().lem_batch_bind_elevation(b, _ptr(h)), "lem_batch_bind_elevation")
+
+
+def lem_batch_set_config(b, block_threads, items_per_thread):
+    _check(lib().lem_batch_set_config(b, block_threads, items_per_thread),
+           "lem_batch_set_config")
+
+
+def lem_batch_step(b, nsteps):
+    _check(lib().lem_batch_step(b, nsteps), "lem_batch_step")
+
+
+def lem_batch_sync(b):
+    _check(lib().lem_batch_sync(b), "lem_batch_sync")
+
+
+BATCH_CONFIGS = [(256, 4), (256, 8), (512, 4), (512, 8), (1024, 4), (1024, 8)]
+
+
+class Batch:
+    """R independent FP32 grids advanced together (packed elevations)."""
+
+    def __init__(self, surfaces, dx, K, m, U, dt, stream=None):
+        import numpy as np
+        R = len(surfaces)
+        bc = lambda v: list(v) if hasattr(v, "__len__") else [v] * R  # noqa: E731
+        self.shapes = [s.shape for s in surfaces]
+        self.b = lem_batch_create([s.shape[1] for s in surfaces], [s.shape[0] for s in surfaces],
+                                  bc(dx), bc(K), bc(m), bc(U), bc(dt))
+        self.R = R
+        self.offsets = lem_batch_offsets(self.b, R)
+        flat = np.concatenate([np.asarray(s, np.float32).ravel() for s in surfaces])
+        self.h = torch.tensor(flat, device="cuda")
+        lem_batch_set_stream(self.b, stream)
+        lem_batch_bind_elevation(self.b, self.h)
+
+    def surface(self, r):
+        ny, nx = self.shapes[r]
+        return self.h[self.offsets[r]:self.offsets[r + 1]].view(ny, nx)
+
+    def set_config(self, block_threads, items_per_thread):
+        lem_batch_set_config(self.b, block_threads, items_per_thread)
+
+    def step(self, nsteps=1):
+        lem_batch_step(self.b, nsteps)
+
+    def sync(self):
+        lem_batch_sync(self.b)
+
+    def close(self):
+        if self.b:
+            lem_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def lem_step_noalloc(h, dx, K, m, U, dt, nsteps, stream=None):

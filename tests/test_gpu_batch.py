@@ -1,0 +1,80 @@
+"""The batched form: every realization advanced in one launch must equal the
+same grid advanced alone by the FP32 single-grid path (identical arithmetic),
+for every kernel shape, and stay within the FP32 bound of the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_02977_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _realizations(R=11, seed=4):
+    u = synth.uniform01(seed, 4 * R).reshape(R, 4)
+    shapes = [(int(3 + u[r, 0] * 300), int(3 + u[r, 1] * 260)) for r in range(R)]
+    shapes[0] = (3, 3)          # degenerate: one interior cell
+    shapes[1] = (513, 7)        # ragged, very wide
+    Ks = [float(10 ** (-6 + 2 * u[r, 2])) for r in range(R)]
+    ms = [float(0.4 + 0.2 * u[r, 3]) for r in range(R)]
+    surfaces = [synth.noise_surface(nx, ny, 1000 + r) for r, (nx, ny) in enumerate(shapes)]
+    return surfaces, Ks, ms
+
+
+def _singles(surfaces, Ks, ms, steps):
+    from paper_1803_02977_gb300 import lem
+    out = []
+    for s, K, m in zip(surfaces, Ks, ms):
+        h = torch.tensor(s.astype(np.float32), device="cuda:0")
+        mdl = lem.Model(h, dx=100.0, K=K, m=m, U=1e-3, dt=1000.0)
+        mdl.step(steps)
+        mdl.sync()
+        out.append(h.cpu().numpy())
+        mdl.close()
+    return out
+
+
+@pytest.mark.parametrize("shape", [(256, 4), (256, 8), (512, 4), (512, 8), (1024, 4), (1024, 8)])
+def test_batch_equals_single_grid_path(shape):
+    from paper_1803_02977_gb300 import lem
+    surfaces, Ks, ms = _realizations()
+    steps = 3
+    b = lem.Batch(surfaces, dx=100.0, K=Ks, m=ms, U=1e-3, dt=1000.0)
+    b.set_config(*shape)
+    b.step(steps)
+    b.sync()
+    want = _singles(surfaces, Ks, ms, steps)
+    for r in range(b.R):
+        assert np.array_equal(b.surface(r).cpu().numpy(), want[r]), f"realization {r}"
+    b.close()
+
+
+def test_batch_per_step_against_oracle():
+    from paper_1803_02977_gb300 import lem
+    surfaces, Ks, ms = _realizations(R=5, seed=9)
+    b = lem.Batch(surfaces, dx=100.0, K=Ks, m=ms, U=1e-3, dt=1000.0)
+    for _ in range(3):
+        before = [b.surface(r).cpu().numpy().astype(np.float64) for r in range(b.R)]
+        b.step(1)
+        b.sync()
+        for r in range(b.R):
+            want, _ = oracle.step(before[r], oracle.params(K=Ks[r], m=ms[r]))
+            got = b.surface(r).cpu().numpy().astype(np.float64)
+            tol = 4 * 2.0 ** -24 * np.maximum(np.abs(want), 1.0)
+            assert np.all(np.abs(got - want) <= tol), f"realization {r}"
+    b.close()
+
+
+def test_autotuner_picks_a_shape_and_keeps_results(tmp_path, monkeypatch):
+    from paper_1803_02977_gb300 import autotune, lem
+    monkeypatch.setenv("LEM_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
+    surfaces, Ks, ms = _realizations(R=7, seed=5)
+    b = lem.Batch(surfaces, dx=100.0, K=Ks, m=ms, U=1e-3, dt=1000.0)
+    h0 = b.h.clone()
+    shape, timings = autotune.tune_batch(b, steps=1)
+    assert tuple(shape) in lem.BATCH_CONFIGS and len(timings) == len(lem.BATCH_CONFIGS)
+    assert torch.equal(b.h, h0)  # tuning restores the elevations
+    shape2, _ = autotune.tune_batch(b, steps=1)  # served from the cache
+    assert tuple(shape2) == tuple(shape)
+    b.close()
