@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--flush-mib", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-phases", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP32, 10000^2, batch and adjoint measurements")
+    ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -334,6 +337,41 @@ def run_ours(args):
     e2e_value = N * Ke * ws / (float(te.item()) / 1e3)
     me.close()
 
+    forms = None
+    if not args.no_forms:
+        forms = {}
+        plain = N / (ms_per_step / 1e3)
+        if args.workload == "grid2048_f64":
+            ms32 = time_grid(lem, synth.workload("grid2048_f32"), min(K, 30), 3, flush, dev)
+            v32 = N / (float(np.mean(ms32)) / 1e3)
+            forms["fp32_same_grid"] = {"workload": "grid2048_f32", "ms_per_step": float(np.mean(ms32)),
+                                       "value": v32, "vs_plain_fp64": v32 / plain}
+        w10 = synth.workload("grid10000_f32")
+        ms10 = time_grid(lem, w10, 5, 2, flush, dev)
+        a10 = sum(algo_bytes(4, 8).values()) * w10.cells / (float(np.mean(ms10)) / 1e3) / 1e9
+        forms["grid10000_f32"] = {"ms_per_step": float(np.mean(ms10)),
+                                  "value": w10.cells / (float(np.mean(ms10)) / 1e3),
+                                  "achieved_gbs": a10,
+                                  "frac_of_measured_hbm": a10 / measured_peaks()["hbm_gbs"],
+                                  "paper_rb_gpu_p100_cell_steps_per_s": 1e8 * 120 / 70.0}
+        del flush
+        torch.cuda.empty_cache()
+        bt = measure_batch(lem, args.batch_steps, ws, rank, dev)
+        t = torch.tensor([bt["ms"], bt["plain_fp64_sample"]["ms"]], dtype=torch.float64,
+                         device=dev)
+        cs = torch.tensor([bt["cell_steps"], bt["plain_fp64_sample"]["cells"] * bt["steps"]],
+                          dtype=torch.float64, device=dev)
+        if ws > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dist.all_reduce(cs)
+        bt["value"] = float(cs[0]) / (float(t[0]) / 1e3)
+        bt["plain_fp64_sample"]["value"] = float(cs[1]) / (float(t[1]) / 1e3)
+        bt["vs_plain_fp64"] = bt["value"] / bt["plain_fp64_sample"]["value"]
+        bt["ranks"] = ws
+        forms["batch512_f32"] = bt
+        if rank == 0:
+            forms["adjoint_grid1024_f64"] = measure_adjoint(lem, dev)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(w, args.cpu_seconds)
@@ -357,13 +395,119 @@ def run_ours(args):
             "roofline": roofline, "phases": phases, "timeline": timeline, "clocks": clk,
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": N * P,
                     "d2h_bytes_per_step": N * P, "steps": Ke},
-            "gpu_launches": K, "cpu_baseline": cpu}
+            "gpu_launches": K, "cpu_baseline": cpu, "forms": forms}
     mdl.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def time_grid(lem, w, steps, warmup, flush, dev):
+    """Per-step device times (ms) of `steps` single-step launches on workload
+    w, L2 flushed between steps; returns (step_ms, final levels)."""
+    import torch
+    P = 8 if w.dtype == "f64" else 4
+    count_bits = 64 if w.area_dtype == "i64" else 32
+    h = torch.tensor(w.initial().astype(np.float64 if P == 8 else np.float32), device=dev)
+    mdl = lem.Model(h, dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt, count_bits=count_bits)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        mdl.step(1)
+        flush.zero_()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    for e0, e1 in ev:
+        e0.record(stream)
+        mdl.step(1)
+        e1.record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    mdl.sync()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    mdl.close()
+    return ms
+
+
+def measure_batch(lem, steps, ws, rank, dev, count=512, sample_every=8):
+    """The 512-realization FP32 batch in one launch (autotuned shape), this
+    rank's LPT shard, against the plain FP64 path run one grid at a time on
+    every sample_every-th realization of the shard."""
+    import torch
+    from paper_1803_02977_gb300 import autotune, sharding, synth
+    bw = synth.batch_workload(count=count)
+    sizes = [s * s for s in bw.sides]
+    mine = sharding.lpt_partition(sizes, ws)[rank]
+    surfaces = [bw.initial(r) for r in mine]
+    B = lem.Batch(surfaces, dx=bw.dx, K=[bw.K[r] for r in mine], m=[bw.m[r] for r in mine],
+                  U=bw.U, dt=bw.dt)
+    shape, tune_ms = autotune.tune_batch(B, steps=1)
+    B.step(1)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    B.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    B.sync()
+    ms = e0.elapsed_time(e1)
+    cells = sum(sizes[r] for r in mine)
+    B.close()
+    del B
+    # plain FP64 path, one grid at a time, on a sample of the shard
+    sample = mine[::sample_every]
+    plain_ms, plain_cells = 0.0, 0
+    for r in sample:
+        h = torch.tensor(bw.initial(r), device=dev)
+        mdl = lem.Model(h, dx=bw.dx, K=bw.K[r], m=bw.m[r], U=bw.U, dt=bw.dt)
+        mdl.step(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        mdl.step(steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_ms += a.elapsed_time(b)
+        plain_cells += sizes[r]
+        mdl.close()
+    return {"ms": ms, "cells": cells, "cell_steps": cells * steps, "realizations": len(mine),
+            "steps": steps, "shape": list(shape),
+            "autotune_ms_per_step": {k: round(v, 3) for k, v in tune_ms.items()},
+            "plain_fp64_sample": {"realizations": len(sample), "cells": plain_cells,
+                                  "ms": plain_ms,
+                                  "value": plain_cells * steps / (plain_ms / 1e3)}}
+
+
+def measure_adjoint(lem, dev, nsteps=50, ckpt=10):
+    """Gradient of sum((h_T - h_obs)^2) wrt the uplift field and K on the
+    1024 x 1024 FP64 adjoint workload: forward + checkpointed adjoint."""
+    import torch
+    from paper_1803_02977_gb300 import autodiff, synth
+    w = synth.workload("grid1024_adjoint")
+    h0 = torch.tensor(w.initial(), device=dev)
+    xi = torch.tensor(synth.signed_field(w.nx, w.ny, 6), device=dev)
+    U = torch.full_like(h0, w.U)
+    obs = h0.clone()
+    m_obs = lem.Model(obs, dx=w.dx, K=1.2 * w.K, m=w.m, U=0.0, dt=w.dt)
+    m_obs.set_uplift_field(U * (1.0 + 0.1 * xi))
+    m_obs.step(nsteps)
+    m_obs.sync()
+    m_obs.close()
+    Ut = U.clone().requires_grad_(True)
+    Kt = torch.tensor(w.K, dtype=torch.float64, device=dev, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hT = autodiff.run(h0, Ut, Kt, nsteps, ckpt_every=ckpt, dx=w.dx, m=w.m, dt=w.dt)
+    loss = torch.sum((hT - obs) ** 2)
+    loss.backward()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return {"grid": [w.nx, w.ny], "steps": nsteps, "ckpt_every": ckpt, "wall_ms": el * 1e3,
+            "loss": loss.item(), "dL_dK": Kt.grad.item(),
+            "gradient_cell_steps_per_s": w.nx * w.ny * nsteps / el}
 
 
 def traced_step(lem, mdl, flush):
@@ -387,8 +531,15 @@ def traced_step(lem, mdl, flush):
     out = {"receivers": 0.0, "levels": 0.0, "accumulate": 0.0, "erode": 0.0}
     barriers = {"wide_levels": 0, "narrow_runs": 0}
     for (t0, _, _), (t1, ph, lvl) in zip(tr[:-1], tr[1:]):
-        if ph == "block0_done":  # block 0 reached barrier 1, 2 (receivers) or 3 (levels)
-            ph = "levels" if lvl == 3 else "receivers"
+        if ph == "block0_done":
+            # block 0 reached barrier 1, 2 (receivers) or 3 (levels), or
+            # finished a private level of expansion (0x1000+) / accumulation (0x2000+)
+            if lvl >= 0x2000:
+                ph = "accumulate"
+            elif lvl >= 0x1000 or lvl == 3:
+                ph = "levels"
+            else:
+                ph = "receivers"
         out[group.get(ph, ph if ph in out else "receivers")] += (t1 - t0) / 1e3
         if ph.endswith("_wide"):
             barriers["wide_levels"] += 1
