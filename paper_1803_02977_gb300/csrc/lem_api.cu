@@ -290,7 +290,11 @@ int lem_create_ex(lem_ctx** out, const lem_params* pin) {
     // private queue share: twice the fair share of cells, at least 4096
     const long long fair = ((long long)c->N + c->grid - 1) / c->grid;
     c->pcap = (int)(2 * fair > 4096 ? 2 * fair : 4096);
-    e = cudaMalloc(&c->code, N);
+    // receiver codes with kCodeGuard bytes of 0xFF on both sides (never a
+    // valid code): word loads of neighbouring rows stay in bounds
+    e = cudaMalloc(&c->code_base, N + 2 * kCodeGuard);
+    if (e == cudaSuccess) e = cudaMemset(c->code_base, 0xFF, N + 2 * kCodeGuard);
+    c->code = c->code_base + kCodeGuard;
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->mask, N);
   if (e == cudaSuccess) e = cudaMalloc(&c->queue, N * sizeof(int));
@@ -331,7 +335,7 @@ int lem_create_ex(lem_ctx** out, const lem_params* pin) {
 
 void lem_destroy(lem_ctx* c) {
   if (!c) return;
-  cudaFree(c->code);
+  cudaFree(c->code_base);
   cudaFree(c->mask);
   cudaFree(c->queue);
   cudaFree(c->levels);

@@ -14,7 +14,8 @@ struct lem_ctx {
   int device = 0;
   void* h = nullptr;
   const double* Uf = nullptr;
-  uint8_t* code = nullptr;
+  uint8_t* code = nullptr;       // code_base + kCodeGuard
+  uint8_t* code_base = nullptr;  // allocation with guard bytes
   uint8_t* mask = nullptr;
   int* queue = nullptr;
   int* levels = nullptr;

@@ -55,7 +55,7 @@ __device__ int forest_receivers(const ForestGrid& g, ForestSmem<BD, PI>& s) {
       int cd = kEdge;
       if (c < w1) {
         const bool perim = (x == 0 || y == 0 || x == nx - 1 || y == ny - 1);
-        cd = perim ? kEdge : receiver_code(g.h, c, nx);
+        cd = perim ? kEdge : receiver_of(g.h, c, nx);
         g.code[c] = (uint8_t)cd;
       }
       wcnt += __popc(__ballot_sync(0xffffffffu, c < w1 && no_receiver(cd)));

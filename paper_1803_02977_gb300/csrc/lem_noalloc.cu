@@ -38,7 +38,7 @@ constexpr size_t kOffPartial = kOffState + align256(sizeof(DevState));
 constexpr size_t kOffFtab = kOffPartial + align256(sizeof(int) * kMaxBlocks);
 constexpr size_t kOffGtab = kOffFtab + align256(sizeof(double2) * 2 * kTableN);
 constexpr size_t kOffCode = kOffGtab + align256(sizeof(float) * 2 * kTableN);
-constexpr size_t kOffMask = kOffCode + align256(kMaxCells);
+constexpr size_t kOffMask = kOffCode + align256(kMaxCells + 2 * kCodeGuard);
 constexpr size_t kOffQueue = kOffMask + align256(kMaxCells);
 constexpr size_t kOffLevels = kOffQueue + align256(sizeof(int) * kMaxCells);
 constexpr size_t kOffCnt = kOffLevels + align256(sizeof(int) * (kMaxCells + 2));
@@ -58,9 +58,14 @@ unsigned char* g_scratch_addr[kMaxDevices] = {};
 // Per-call set-up inside the scratch: clear the status and barrier words
 // (they must start at zero) and fill the erosion tables for this call's
 // parameters, with the same operation order as the step kernel expects.
-__global__ void noalloc_prepare_kernel(unsigned char* base, double Kdt, double m, double dx,
-                                       double dxd, double area_scale) {
+__global__ void noalloc_prepare_kernel(unsigned char* base, int N, double Kdt, double m,
+                                       double dx, double dxd, double area_scale) {
   DevState* st = reinterpret_cast<DevState*>(base + kOffState);
+  // guard bytes around this call's receiver codes: never a valid code
+  if (blockIdx.x == 0 && threadIdx.x < 2 * kCodeGuard) {
+    const int i = threadIdx.x;
+    base[kOffCode + (i < kCodeGuard ? i : kCodeGuard + N + (i - kCodeGuard))] = 0xFF;
+  }
   double2* Ftab = reinterpret_cast<double2*>(base + kOffFtab);
   float* gtab = reinterpret_cast<float*>(base + kOffGtab);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -124,7 +129,7 @@ extern "C" LEM_API int lem_step_noalloc(int nx, int ny, double* dev_h, double dx
   if (grid > kMaxBlocks) grid = kMaxBlocks;
 
   const double Kdt = K * dt, dxd = dx * kSqrt2, area = dx * dx;
-  noalloc_prepare_kernel<<<64, 256, 0, s>>>(base, Kdt, m, dx, dxd, area);
+  noalloc_prepare_kernel<<<64, 256, 0, s>>>(base, nx * ny, Kdt, m, dx, dxd, area);
   e = cudaGetLastError();
   if (e != cudaSuccess) return status_of(e);
 
@@ -142,7 +147,7 @@ extern "C" LEM_API int lem_step_noalloc(int nx, int ny, double* dev_h, double dx
   a.dx = dx;
   a.dxd = dxd;
   a.area_scale = area;
-  a.code = base + kOffCode;
+  a.code = base + kOffCode + kCodeGuard;
   a.mask = base + kOffMask;
   a.queue = reinterpret_cast<int*>(base + kOffQueue);
   a.levels = reinterpret_cast<int*>(base + kOffLevels);

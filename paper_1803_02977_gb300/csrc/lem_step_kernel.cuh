@@ -75,6 +75,7 @@ struct StepArgs {
   int frozen;           // receivers frozen: codes are inputs, not recomputed
 };
 
+constexpr int kCodeGuard = 16;     // 0xFF guard bytes on each side of the code array
 constexpr int kBD = 1024;          // threads per block: one block per SM
 constexpr int kWarps = kBD / 32;
 constexpr int kNarrow = kBD;       // a device-wide level this small runs in block 0
@@ -208,6 +209,71 @@ __device__ __forceinline__ int receiver_code(const HT* __restrict__ h, int c, in
                             (double)v[7]);
 }
 
+// Alg 1 for FP32 elevations: the same result as receiver_code<float>, with
+// the group minima taken by float min/max (all nine values non-negative and
+// finite, so min is exact and equality picks the lowest k).  The runner-up
+// check is needed only when a minimum is 0 or more than 27 binades below h_c
+// (otherwise distinct floats are always more than 4 FP64 ulps of h_c apart).
+__device__ __forceinline__ bool f32_group_safe(const float* v, const int* ks, float m, float hc) {
+  using B = Bits<float>;
+  const unsigned bm = B::of(m), bc = B::of(hc);
+  if (bm != 0 && (int)(bc >> 23) - max((int)(bm >> 23), 1) <= 27) return true;
+  unsigned r = bc;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const unsigned x = B::of(v[ks[i]]);
+    if (x > bm && x < r) r = x;
+  }
+  return no_rounding_merge<float>(bm, r, bc);
+}
+
+__device__ __forceinline__ int receiver_code_f32(const float* __restrict__ h, int c, int nx) {
+  float v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = h[c + nbr_off(k, nx)];
+  const float hc = h[c];
+  unsigned worst = Bits<float>::of(hc);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) worst = max(worst, Bits<float>::of(v[k]));
+  if (worst < Bits<float>::kInf) {
+    const float mC = fminf(fminf(v[1], v[3]), fminf(v[4], v[6]));
+    const float mD = fminf(fminf(v[0], v[2]), fminf(v[5], v[7]));
+    const bool hasC = mC < hc, hasD = mD < hc;
+    if (!hasC && !hasD) return kSink;
+    const int kC = v[1] == mC ? 1 : (v[3] == mC ? 3 : (v[4] == mC ? 4 : 6));
+    const int kD = v[0] == mD ? 0 : (v[2] == mD ? 2 : (v[5] == mD ? 5 : 7));
+    const int cks[4] = {1, 3, 4, 6}, dks[4] = {0, 2, 5, 7};
+    if ((!hasC || f32_group_safe(v, cks, mC, hc)) && (!hasD || f32_group_safe(v, dks, mD, hc))) {
+      if (!hasD) return kC;
+      if (!hasC) return kD;
+      const float sCf = __fsub_rn(hc, mC);
+      const float sDf = __fmul_rn(__fsub_rn(hc, mD), 0.70710677f);
+      if (fminf(sCf, sDf) > 1e-30f) {
+        if (sCf > __fmul_rn(sDf, 1.000003814697265625f)) return kC;
+        if (sDf > __fmul_rn(sCf, 1.000003814697265625f)) return kD;
+      }
+      const double hcd = (double)hc;
+      const double sC = __dsub_rn(hcd, (double)mC);
+      const double sD = __dmul_rn(__dsub_rn(hcd, (double)mD), kInvSqrt2);
+      const long long bC = __double_as_longlong(sC), bD = __double_as_longlong(sD);
+      if (bC > bD) return kC;
+      if (bD > bC) return kD;
+      return min(kC, kD);
+    }
+  }
+  return receiver_code_slow((double)hc, (double)v[0], (double)v[1], (double)v[2], (double)v[3],
+                            (double)v[4], (double)v[5], (double)v[6], (double)v[7]);
+}
+
+template <typename HT>
+__device__ __forceinline__ int receiver_of(const HT* __restrict__ h, int c, int nx) {
+  if constexpr (sizeof(HT) == 4) {
+    return receiver_code_f32(h, c, nx);
+  } else {
+    return receiver_code(h, c, nx);
+  }
+}
+
 // Alg 2 for one cell (perimeter included): bit k set iff neighbour k is in
 // the grid and its receiver code points back at this cell (code 7-k).
 __device__ __forceinline__ int donor_mask(const uint8_t* __restrict__ code, int c, int x, int y,
@@ -226,6 +292,50 @@ __device__ __forceinline__ int donor_mask(const uint8_t* __restrict__ code, int 
     }
   }
   return msk;
+}
+
+// The 12 receiver-code bytes around code[p], read as three aligned words;
+// at(dx) returns the 4 codes code[p+dx .. p+dx+3] (dx in {-1, 0, 1}) as one
+// word.  The code array carries 16 guard bytes of 0xFF on both sides, so the
+// loads stay in bounds for every row with a row above and below.
+struct CodeRow {
+  unsigned w0, w1, w2;
+  int off;  // byte offset of code[p-1] within w0
+  __device__ __forceinline__ CodeRow(const uint8_t* code, int p) {
+    const int q = p - 1;
+    const int al = q & ~3;
+    off = q - al;
+    const unsigned* wp = reinterpret_cast<const unsigned*>(code + al);
+    w0 = wp[0];
+    w1 = wp[1];
+    w2 = wp[2];
+  }
+  __device__ __forceinline__ unsigned at(int dx) const {
+    const int s = off + 1 + dx;  // 0..5
+    return s < 4 ? __funnelshift_r(w0, w1, 8 * s) : __funnelshift_r(w1, w2, 8 * (s - 4));
+  }
+};
+
+// Alg 2 for the four cells c..c+3 of one row band (c a multiple of 4, all
+// four with a row above and below): bit k of byte i of *mword is set iff
+// neighbour k of cell c+i drains into it (code 7-k); *cword gets their codes.
+// Neighbours that wrap across a row end are perimeter cells (code 9) or guard
+// bytes (0xFF), which never match.
+__device__ __forceinline__ void donor_masks4(const uint8_t* __restrict__ code, int c, int nx,
+                                             unsigned* mword, unsigned* cword) {
+  const CodeRow up(code, c - nx), mid(code, c), dn(code, c + nx);
+  unsigned m = 0;
+  const unsigned ones = 0x01010101u;
+  m |= __vcmpeq4(up.at(-1), 7u * ones) & (0x01u * ones);   // k=0 NW
+  m |= __vcmpeq4(up.at(0), 6u * ones) & (0x02u * ones);    // k=1 N
+  m |= __vcmpeq4(up.at(1), 5u * ones) & (0x04u * ones);    // k=2 NE
+  m |= __vcmpeq4(mid.at(-1), 4u * ones) & (0x08u * ones);  // k=3 W
+  m |= __vcmpeq4(mid.at(1), 3u * ones) & (0x10u * ones);   // k=4 E
+  m |= __vcmpeq4(dn.at(-1), 2u * ones) & (0x20u * ones);   // k=5 SW
+  m |= __vcmpeq4(dn.at(0), 1u * ones) & (0x40u * ones);    // k=6 S
+  m |= __vcmpeq4(dn.at(1), 0u * ones) & (0x80u * ones);    // k=7 SE
+  *mword = m;
+  *cword = mid.at(0);
 }
 
 // ---- Alg 5 + Alg 6 -------------------------------------------------------------
@@ -379,9 +489,10 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
   const unsigned G = gridDim.x;
   const int b = blockIdx.x, t = threadIdx.x, w = t >> 5, lane = t & 31;
   const int nx = a.nx, ny = a.ny, N = a.N;
-  const int chunk = (N + (int)G - 1) / (int)G;
+  // chunk and warp ranges start at multiples of 4 cells (128 per warp round)
+  const int chunk = ((N + (int)G - 1) / (int)G + 127) & ~127;
   const int c0 = min(N, b * chunk), c1 = min(N, c0 + chunk);
-  const int wchunk = ((c1 - c0 + kWarps - 1) / kWarps + 31) & ~31;
+  const int wchunk = ((c1 - c0 + kWarps - 1) / kWarps + 127) & ~127;
   const int w0 = min(c1, c0 + w * wchunk), w1 = min(c1, w0 + wchunk);
   if (b == 0 && t == 0) a.st->private_overflow = 0;
 
@@ -406,7 +517,7 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
       if (c < w1) {
         if (!a.frozen) {
           const bool perim = (x == 0 || y == 0 || x == nx - 1 || y == ny - 1);
-          code = perim ? kEdge : receiver_code(a.h, c, nx);
+          code = perim ? kEdge : receiver_of(a.h, c, nx);
           a.code[c] = (uint8_t)code;
         } else {
           code = a.code[c];
@@ -444,44 +555,50 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
   uint8_t* pqm = a.pqm + (size_t)b * a.pcap;
   uint8_t* pqk = a.pqk + (size_t)b * a.pcap;
   {
-    int x = w0 + lane, y = 0;
-    if (w0 < w1) {
-      y = x / nx;
-      x -= y * nx;
-    }
+    // Each lane takes 4 consecutive cells (w0 is a multiple of 4): their
+    // masks are built as one 32-bit word, byte by byte in parallel.
     int run = wpre;
-    for (int base = w0; base < w1; base += 32) {
-      const int c = base + lane;
-      const int cp = c + 64;
-      if (cp < w1 && cp > nx && cp + nx < N) {
-        prefetch_l1(a.code + (cp - nx));
-        prefetch_l1(a.code + cp);
-        prefetch_l1(a.code + (cp + nx));
-      }
-      bool f = false;
-      int msk = 0, cd = kEdge;
-      if (c < w1) {
-        msk = donor_mask(a.code, c, x, y, nx, ny);
-        a.mask[c] = (uint8_t)msk;
-        cd = a.code[c];
-        f = no_receiver(cd);
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, f);
-      if (f) {
-        const int pos = run + __popc(bal & ((1u << lane) - 1u));
-        a.queue[prefix + pos] = c;
-        if (pos < a.pcap) {
-          pq[pos] = c;
-          pqm[pos] = (uint8_t)msk;
-          pqk[pos] = (uint8_t)cd;
+    for (int base = w0; base < w1; base += 128) {
+      const int c = base + 4 * lane;
+      const int nv = max(0, min(4, w1 - c));  // cells of this lane in range
+      unsigned mword = 0, cword = 0;           // masks, codes (byte i: cell c+i)
+      if (nv == 4 && c >= nx && c + 3 + nx < N) {
+        donor_masks4(a.code, c, nx, &mword, &cword);
+        *reinterpret_cast<unsigned*>(a.mask + c) = mword;
+      } else {
+        for (int i = 0; i < nv; ++i) {
+          const int ci = c + i, y = ci / nx, x = ci - y * nx;
+          const unsigned msk = donor_mask(a.code, ci, x, y, nx, ny);
+          a.mask[ci] = (uint8_t)msk;
+          mword |= msk << (8 * i);
+          cword |= (unsigned)a.code[ci] << (8 * i);
         }
       }
-      run += __popc(bal);
-      x += 32;
-      while (x >= nx) {
-        x -= nx;
-        ++y;
+      // cells without receiver (code >= 8): 0xFF bytes, in-range cells only
+      const unsigned valid = nv >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nv)) - 1u);
+      const unsigned f = __vcmpgeu4(cword, 0x08080808u) & valid;
+      const int cnt = __popc(f) >> 3;
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
       }
+      int pos = run + incl - cnt;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if ((f >> (8 * i)) & 1u) {
+          const int ci = c + i;
+          a.queue[prefix + pos] = ci;
+          if (pos < a.pcap) {
+            pq[pos] = ci;
+            pqm[pos] = (uint8_t)(mword >> (8 * i));
+            pqk[pos] = (uint8_t)(cword >> (8 * i));
+          }
+          ++pos;
+        }
+      }
+      run += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
   if (b == 0 && t == 0) {
