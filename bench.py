@@ -20,8 +20,11 @@ ranks divided by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -381,8 +384,10 @@ def run_ours(args):
     per_cell = sum(ab.values())
     achieved = per_cell * N / (ms_per_step / 1e3) / 1e9
     peak = peaks.get("hbm_gbs")
+    traffic, traffic_src = profiled_traffic(w.name)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if peak else None, "traffic": None,
+                "frac": (achieved / peak) if peak else None, "traffic": traffic,
+                "traffic_source": traffic_src,
                 "kernel": "lem_step_kernel (one cooperative launch per step)",
                 "algo_bytes_per_cell_step": per_cell,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peak else None}
@@ -549,6 +554,34 @@ def traced_step(lem, mdl, flush):
            for (t0, _, _), (t1, ph, lvl) in zip(tr[:-1], tr[1:])][:64]
     return {"us": out, "total_us": (tr[-1][0] - tr[0][0]) / 1e3, "segments": len(tr) - 1,
             **barriers, "raw": raw}
+
+
+def kernel_source_hash():
+    """sha256 over the kernel sources and the C-ABI header (name + bytes,
+    in sorted order); a committed ncu summary records the hash it was taken
+    at, so its DRAM figures are only reported while the kernels match."""
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1803_02977_gb300", "csrc", "*.cu*")))
+    for p in files + [os.path.join(ROOT, "include", "lem.h")]:
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(workload):
+    """DRAM bytes (read + write) per launch of the step kernel from the
+    committed ncu summary of this workload, or None when there is none or
+    the kernel sources changed since it was captured."""
+    want = kernel_source_hash()
+    for p in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(p) as f:
+            kv = dict(re.findall(r"^(traffic_bytes_per_launch|workload|source_sha256): (\S+)$",
+                                 f.read(), re.M))
+        if kv.get("workload") == workload and kv.get("source_sha256") == want \
+                and "traffic_bytes_per_launch" in kv:
+            return int(kv["traffic_bytes_per_launch"]), os.path.relpath(p, ROOT)
+    return None, None
 
 
 def measured_peaks():
