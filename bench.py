@@ -273,6 +273,10 @@ def run_ours(args):
     value = N * K * ws / (tot_ms / 1e3)
     ms_per_step = tot_ms / K
 
+    # which tier handled the cells (warp tiles, block queues, device-wide)
+    tiers = lem.lem_tier_stats(mdl.ctx)
+    tier_frac = [x / max(1, sum(tiers)) for x in tiers]
+
     # one traced step after the timed region: in-kernel time per phase
     timeline = traced_step(lem, mdl, flush)
 
@@ -397,7 +401,10 @@ def run_ours(args):
             "config": config_of(w, args), "levels_after": int(L),
             "step_ms_min_median_max": [min(step_ms), float(np.median(step_ms)), max(step_ms)],
             "wall_s_timed_region": t_wall,
-            "roofline": roofline, "phases": phases, "timeline": timeline, "clocks": clk,
+            "roofline": roofline, "phases": phases, "timeline": timeline,
+            "tier_cell_fraction": {"warp_tiles": tier_frac[0], "block_queues": tier_frac[1],
+                                   "device_wide": tier_frac[2]},
+            "clocks": clk,
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": N * P,
                     "d2h_bytes_per_step": N * P, "steps": Ke},
             "gpu_launches": K, "cpu_baseline": cpu, "forms": forms}
@@ -516,44 +523,38 @@ def measure_adjoint(lem, dev, nsteps=50, ckpt=10):
 
 
 def traced_step(lem, mdl, flush):
-    """One step with device-side tracing: microseconds spent in each phase
-    (segments between consecutive device-wide barriers, as seen by block 0)."""
+    """One tiered step with device-side tracing, as seen by block 0: the
+    microseconds between consecutive trace points, grouped by what ended
+    them (block 0's own work, or the wait at a device-wide barrier)."""
     lem.lem_trace_enable(mdl.ctx, 1 << 16)
     flush.zero_()
-    mdl.step(2)  # the first step ends at a device-wide barrier: all blocks done
+    mdl.step(2)  # the second step's start marks the end of the first
     tr = lem.lem_trace_read(mdl.ctx, 1 << 16)
     lem.lem_trace_enable(mdl.ctx, 0)
-    ends = [i for i, e in enumerate(tr) if e[1] == "step_end"]
-    if ends:
-        tr = tr[:ends[0] + 1]
+    starts = [i for i, e in enumerate(tr) if e[1] == "start"]
+    if len(starts) >= 2:
+        tr = tr[:starts[1] + 1]
     if len(tr) < 2:
         return None
-    group = {"receivers": "receivers", "level0": "receivers", "bfs_wide": "levels",
-             "bfs_narrow": "levels", "acc_wide": "accumulate", "acc_narrow": "accumulate",
-             "uplift": "erode", "erode_wide": "erode", "erode_narrow": "erode",
-             "private_levels": "levels", "private_accumulate": "accumulate",
-             "private_erode": "erode", "step_end": "erode"}
-    out = {"receivers": 0.0, "levels": 0.0, "accumulate": 0.0, "erode": 0.0}
-    barriers = {"wide_levels": 0, "narrow_runs": 0}
+    out = {"codes": 0.0, "codes_wait": 0.0, "tiles_warp": 0.0, "tiles_block": 0.0,
+           "tiles_wait": 0.0, "device_tier": 0.0}
+    device_levels = 0
     for (t0, _, _), (t1, ph, lvl) in zip(tr[:-1], tr[1:]):
+        us = (t1 - t0) / 1e3
         if ph == "block0_done":
-            # block 0 reached barrier 1, 2 (receivers) or 3 (levels), or
-            # finished a private level of expansion (0x1000+) / accumulation (0x2000+)
-            if lvl >= 0x2000:
-                ph = "accumulate"
-            elif lvl >= 0x1000 or lvl == 3:
-                ph = "levels"
-            else:
-                ph = "receivers"
-        out[group.get(ph, ph if ph in out else "receivers")] += (t1 - t0) / 1e3
-        if ph.endswith("_wide"):
-            barriers["wide_levels"] += 1
-        elif ph.endswith("_narrow"):
-            barriers["narrow_runs"] += 1
+            key = {1: "codes", 4: "tiles_warp"}.get(lvl, "tiles_block")
+        elif ph == "receivers":
+            key = "codes_wait"
+        elif ph == "tiles_end":
+            key = "tiles_wait"
+        else:
+            key = "device_tier"
+            device_levels += ph.endswith("_wide") or ph.endswith("_narrow")
+        out[key] += us
     raw = [[ph, lvl, round((t1 - t0) / 1e3, 2)]
            for (t0, _, _), (t1, ph, lvl) in zip(tr[:-1], tr[1:])][:64]
     return {"us": out, "total_us": (tr[-1][0] - tr[0][0]) / 1e3, "segments": len(tr) - 1,
-            **barriers, "raw": raw}
+            "device_tier_barrier_runs": device_levels, "raw": raw}
 
 
 def kernel_source_hash():

@@ -174,19 +174,27 @@ LEM_API int lem_set_wait_limit(lem_ctx* ctx, double seconds);
  * the context stays usable.  Exercises the timeout path without a fault. */
 LEM_API int lem_selftest_wait(lem_ctx* ctx);
 
-/* How lem_step runs Algs 3-6.  Mode 0 (default): each thread block expands,
- * accumulates and erodes the trees grown from its own share of the cells
- * without receiver in a private queue, so levels need only block-level
- * barriers (the paper's private queues, Section "Independent Parallelism");
- * if any block's forest exceeds twice its fair share of cells the step is
- * redone on device-wide levels.  Mode 1: device-wide levels only, one grid
- * barrier per level (the paper's level-synchronous queue).  Both give the
- * same elevations; the integer stages are identical. */
+/* How lem_step runs Algs 3-6.  Mode 0 (default): the trees are grown,
+ * accumulated and eroded privately (the paper's private queues, Section
+ * "Independent Parallelism").  The grid is cut into 32x8 tiles; a warp takes
+ * the trees rooted in one tile and runs Algs 3-6 on them in its own slice of
+ * shared memory with warp barriers only (up to 384 cells and 127 levels with
+ * FP64 elevations, 512 cells with FP32).  Trees that do not fit go to their
+ * thread block's private queue in global memory (block barriers; up to twice
+ * the block's fair share of cells and 2048 levels), and what still does not
+ * fit to device-wide levels (one grid barrier per level).  Mode 1:
+ * device-wide levels only (the paper's level-synchronous queue).  Both give
+ * the same elevations; the integer stages are identical. */
 LEM_API int lem_set_step_mode(lem_ctx* ctx, int mode);
 
-/* Number of lem_step steps completed on block-private queues and on
- * device-wide levels since the context was created (synchronises). */
+/* Number of lem_step steps completed without and with device-wide levels
+ * since the context was created (synchronises). */
 LEM_API int lem_step_stats(lem_ctx* ctx, int64_t* private_steps, int64_t* device_wide_steps);
+
+/* Cells handled by lem_step (mode 0) since the context was created, per
+ * tier: cells[0] warp tiles in shared memory, cells[1] block-private queues,
+ * cells[2] device-wide levels (synchronises).  cells must hold 3 entries. */
+LEM_API int lem_tier_stats(lem_ctx* ctx, int64_t* cells);
 
 /* Device-side tracing of the step kernel's timeline: with capacity > 0,
  * later launches record, after every device-wide barrier, the GPU global

@@ -171,6 +171,8 @@ StepArgs<HT, CT> make_args(lem_ctx* c, int phases, int nsteps) {
   a.pqf = c->pqf;
   a.cntq = (CT*)c->cntq;
   a.pcap = c->pcap;
+  a.tiles_x = (c->p.nx + kTileW - 1) / kTileW;
+  a.ntiles = a.tiles_x * ((c->p.ny + kTileH - 1) / kTileH);
   a.Udt = c->p.U * c->p.dt;
   a.Udt_f = (float)(c->p.U * c->p.dt);
   a.phases = phases;
@@ -457,7 +459,7 @@ int lem_step(lem_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return LEM_EINVAL;
   if (!c->h) return LEM_ESTATE;
   if (nsteps == 0) return LEM_OK;
-  int rc = launch_step(c, c->mode == 0 ? (kPhRec | kPhPrivate) : kPhAll, nsteps);
+  int rc = launch_step(c, c->mode == 0 ? kPhTiles : kPhAll, nsteps);
   if (rc != LEM_OK) return rc;
   // A frozen graph's codes and masks stay current; the device-wide queue and
   // counts are current only if the device-wide form ran (mode 1).
@@ -519,6 +521,16 @@ int lem_step_stats(lem_ctx* c, int64_t* private_steps, int64_t* device_wide_step
                       cudaMemcpyDeviceToHost));
   if (private_steps) *private_steps = v[0];
   if (device_wide_steps) *device_wide_steps = v[1];
+  return LEM_OK;
+}
+
+int lem_tier_stats(lem_ctx* c, int64_t* cells) {
+  if (!c || !cells) return LEM_EINVAL;
+  LEM_CUDA(cudaStreamSynchronize(c->stream));
+  unsigned long long v[3] = {0, 0, 0};
+  LEM_CUDA(cudaMemcpy(v, (char*)c->st + offsetof(DevState, tier_cells), sizeof(v),
+                      cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 3; ++i) cells[i] = (int64_t)v[i];
   return LEM_OK;
 }
 

@@ -28,10 +28,9 @@ constexpr int kPhLev = 2;     // Alg 3 breadth-first levels
 constexpr int kPhAcc = 4;     // Alg 4 accumulation
 constexpr int kPhEro = 8;     // Alg 5 + Alg 6
 constexpr int kPhAll = 15;
-// Algs 3-6 on block-private queues (each block expands, accumulates and
-// erodes the trees grown from its own cells without receiver), falling back
-// to the device-wide levels when a block's forest outgrows its share.
-constexpr int kPhPrivate = 16;
+// Algs 3-6 on warp-private forests in shared memory, with block-private and
+// device-wide tiers for trees that do not fit (lem_step's default form).
+constexpr int kPhTiles = 32;
 
 __host__ __device__ __forceinline__ int nbr_dx(int k) {
   return (k == 0 || k == 3 || k == 5) ? -1 : ((k == 2 || k == 4 || k == 7) ? 1 : 0);
@@ -59,10 +58,14 @@ struct DevState {
   int selftest_flag;  // never written by anyone: the self-test waits on it
   int trace_cap;      // capacity of trace (entries); 0 = tracing off
   int trace_n;        // entries written since the last read
-  int private_overflow;  // a block's private forest exceeded its capacity
   unsigned long long* trace;  // pairs {globaltimer ns, tag}
-  int private_steps;     // steps completed on block-private queues
-  int global_steps;      // steps that fell back to device-wide levels
+  int private_steps;     // steps completed without device-wide levels
+  int global_steps;      // steps that needed device-wide levels
+  // per-step words of the tiered step, double-buffered by step parity:
+  // roots handed to the device tier, cells handled by all tiers
+  int dev_roots[2];
+  int covered[2];
+  unsigned long long tier_cells[3];  // cells handled by warp, block, device tier
 };
 
 // Trace tags: phase in the high half, level (or 0) in the low half.
@@ -82,6 +85,7 @@ enum TraceTag : int {
   kTrPrivEro = 13 << 16,    // block 0 finished its private erosion
   kTrStepEnd = 14 << 16,    // end-of-step barrier passed
   kTrLocal = 15 << 16,      // block 0 reached the next barrier (low half: which)
+  kTrTilesEnd = 16 << 16,   // warp and block tiers done on every block (barrier passed)
 };
 
 // Record a timestamp (block 0, thread 0 only; no-op when tracing is off).

@@ -164,7 +164,9 @@ extern "C" LEM_API int lem_step_noalloc(int nx, int ny, double* dev_h, double dx
   a.gtab = reinterpret_cast<const float*>(base + kOffGtab);
   a.st = reinterpret_cast<DevState*>(base + kOffState);
   a.partial = reinterpret_cast<int*>(base + kOffPartial);
-  a.phases = kPhRec | kPhPrivate;
+  a.tiles_x = (nx + kTileW - 1) / kTileW;
+  a.ntiles = a.tiles_x * ((ny + kTileH - 1) / kTileH);
+  a.phases = kPhTiles;
   a.nsteps = nsteps;
   a.frozen = 0;
   void* args[] = {&a};

@@ -65,6 +65,7 @@ struct StepArgs {
   int* pqf;             // position of each private-queue entry's first donor
   CT* cntq;             // cell count of each private-queue entry (queue order)
   int pcap;             // entries per block in pq
+  int tiles_x, ntiles;  // warp-tier tiles per row, in total
   CT* cnt;
   const double2* Ftab;  // {F, F/(1+F)} for counts < kTableN: [0,N) cardinal, [N,2N) diagonal
   const float* gtab;    // F/(1+F) rounded to float, same layout
@@ -82,9 +83,18 @@ constexpr int kNarrow = kBD;       // a device-wide level this small runs in blo
 constexpr int kItems = 4;          // items per thread per round in wide loops
 constexpr int kPItems = 8;         // entries per thread per round of a private level
 constexpr int kStage = 16384;      // emitted entries staged in shared memory per round
-// dynamic shared memory of the step kernel: the staging buffer
-constexpr int kDynSmem = kStage * (int)(sizeof(int) + 1);
 constexpr int kMaxPrivLevels = 2048;  // level offsets a private queue may hold
+constexpr int kOvfCap = 256;       // tiles a block keeps for its block tier
+constexpr int kTileW = 32;         // warp-tier tile width: one column per lane
+constexpr int kTileH = 8;          // warp-tier tile height
+constexpr int kWarpBytes = 6144;   // shared memory per warp for its forest
+constexpr int kTileLv = 127;       // levels a warp forest may hold
+constexpr int kTileLvBytes = 256;  // its level offsets, u16 [0, kTileLv]
+// dynamic shared memory of the step kernel: the warps' forests, or (later in
+// the step) the block tier's staging buffer
+constexpr int kDynSmem = kWarps * kWarpBytes > kStage * (int)(sizeof(int) + 1)
+                             ? kWarps * kWarpBytes
+                             : kStage * (int)(sizeof(int) + 1);
 
 // ---- Alg 1: receivers ----------------------------------------------------------
 
@@ -156,13 +166,9 @@ __device__ __forceinline__ bool no_rounding_merge(typename Bits<HT>::U m, typena
 // neighbour of the group could round to the same slope.  Cells where that
 // check, or non-negative finiteness, fails take the reference form.
 template <typename HT>
-__device__ __forceinline__ int receiver_code(const HT* __restrict__ h, int c, int nx) {
+__device__ __forceinline__ int receiver_code_vals(const HT hcv, const HT* v) {
   using B = Bits<HT>;
   using U = typename B::U;
-  HT v[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) v[k] = h[c + nbr_off(k, nx)];
-  const HT hcv = h[c];
   const U bc = B::of(hcv);
   U mC = bc, mD = bc, rC = bc, rD = bc;  // group minima and runners-up below hc
   int kC = kSink, kD = kSink;
@@ -227,11 +233,7 @@ __device__ __forceinline__ bool f32_group_safe(const float* v, const int* ks, fl
   return no_rounding_merge<float>(bm, r, bc);
 }
 
-__device__ __forceinline__ int receiver_code_f32(const float* __restrict__ h, int c, int nx) {
-  float v[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) v[k] = h[c + nbr_off(k, nx)];
-  const float hc = h[c];
+__device__ __forceinline__ int receiver_code_f32_vals(const float hc, const float* v) {
   unsigned worst = Bits<float>::of(hc);
 #pragma unroll
   for (int k = 0; k < 8; ++k) worst = max(worst, Bits<float>::of(v[k]));
@@ -265,13 +267,24 @@ __device__ __forceinline__ int receiver_code_f32(const float* __restrict__ h, in
                             (double)v[4], (double)v[5], (double)v[6], (double)v[7]);
 }
 
+// Alg 1 for an interior cell of elevation hc with neighbour elevations
+// v[0..7] (k order).
+template <typename HT>
+__device__ __forceinline__ int receiver_from(const HT hc, const HT* v) {
+  if constexpr (sizeof(HT) == 4) {
+    return receiver_code_f32_vals(hc, v);
+  } else {
+    return receiver_code_vals(hc, v);
+  }
+}
+
+// Alg 1 for interior cell c, elevations read from h.
 template <typename HT>
 __device__ __forceinline__ int receiver_of(const HT* __restrict__ h, int c, int nx) {
-  if constexpr (sizeof(HT) == 4) {
-    return receiver_code_f32(h, c, nx);
-  } else {
-    return receiver_code(h, c, nx);
-  }
+  HT v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = h[c + nbr_off(k, nx)];
+  return receiver_from(h[c], v);
 }
 
 // Alg 2 for one cell (perimeter included): bit k set iff neighbour k is in
@@ -478,59 +491,191 @@ struct Shared {
   int chunk[kPItems * kWarps];  // per (slot, warp) donor totals, then offsets
   int chunk_total;
   int plev[kMaxPrivLevels + 1];
+  int tile_next, n_ovf, n0;     // warp tier: next tile; block tier: tiles, roots
+  int ovf_tiles[kOvfCap];
 };
 static_assert(kPItems * kWarps == 8 * 32, "one warp scans the chunk totals 8 per lane");
 
 // ---- phase: Alg 1 receivers, Alg 2 donor masks, level 0 of Alg 3 ---------------
-// Returns false if a barrier was abandoned.  On return *n0 holds the number
-// of this block's cells without receiver (its private level 0).
+
+// Block b's chunk of cells and warp w's sub-chunk of it; both start at
+// multiples of 4 cells (128 per warp round).
+__device__ __forceinline__ void warp_range(int N, int G, int b, int w, int* w0, int* w1) {
+  const int chunk = ((N + G - 1) / G + 127) & ~127;
+  const int c0 = min(N, b * chunk), c1 = min(N, c0 + chunk);
+  const int wchunk = ((c1 - c0 + kWarps - 1) / kWarps + 127) & ~127;
+  *w0 = min(c1, c0 + w * wchunk);
+  *w1 = min(c1, *w0 + wchunk);
+}
+
+// Alg 1 over cells [w0, w1) by one warp (or, for a frozen graph, a read of
+// the codes); returns the number of those cells without receiver.
 template <typename HT, typename CT>
-__device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& s, int* n0) {
+__device__ __forceinline__ int codes_sweep(const StepArgs<HT, CT>& a, int w0, int w1, int lane) {
+  const int nx = a.nx, ny = a.ny, N = a.N;
+  int wcnt = 0;
+  int x = w0 + lane, y = 0;
+  if (w0 < w1) {
+    y = x / nx;
+    x -= y * nx;
+  }
+  for (int base = w0; base < w1; base += 32) {
+    const int c = base + lane;
+    // the three rows two iterations ahead, into L1 (in-grid addresses only)
+    const int cp = c + 64;
+    if (!a.frozen && cp < w1 && cp > nx && cp + nx < N) {
+      prefetch_l1(a.h + (cp - nx));
+      prefetch_l1(a.h + cp);
+      prefetch_l1(a.h + (cp + nx));
+    }
+    int code = kEdge;
+    if (c < w1) {
+      if (!a.frozen) {
+        const bool perim = (x == 0 || y == 0 || x == nx - 1 || y == ny - 1);
+        code = perim ? kEdge : receiver_of(a.h, c, nx);
+        a.code[c] = (uint8_t)code;
+      } else {
+        code = a.code[c];
+      }
+    }
+    wcnt += __popc(__ballot_sync(0xffffffffu, c < w1 && no_receiver(code)));
+    x += 32;
+    while (x >= nx) {
+      x -= nx;
+      ++y;
+    }
+  }
+  return wcnt;
+}
+
+// Algs 1-2 for the tiered step.  A warp owns a strip of kStripOut columns
+// and kStripRows rows at a time.  It first stages the elevations the strip
+// needs (two rows and columns of halo on each side) into its slice of shared
+// memory with asynchronous copies, all in flight at once; then lane l walks
+// down column x0 - 1 + l (lanes 0 and 31 are halo columns) with a 3x3 window
+// in registers.  Receiver codes are computed for the strip's rows and one
+// halo row above and below, so the donor mask of each owned cell (Alg 2)
+// follows from the codes of its 3x3 neighbourhood, exchanged by shuffles.
+// Cells outside the grid count as code 0xFF (no receiver anywhere), which
+// leaves the perimeter cells' masks exact.
+constexpr int kStripOut = 30;                // owned columns per strip (lanes 1..30)
+constexpr int kStripRows = 16;               // owned rows per strip
+constexpr int kStageRows = kStripRows + 4;   // staged rows: two of halo each side
+constexpr int kStageCols = 36;               // staged columns (16-byte aligned start)
+
+template <typename HT>
+__device__ __forceinline__ void cp_async_elem(HT* dst, const HT* src, bool in) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src),
+               "n"((int)sizeof(HT)), "r"(in ? (int)sizeof(HT) : 0)
+               : "memory");
+}
+
+// Stage rows [yb, yb + kStageRows) x columns [xb, xb + kStageCols) of h into
+// S (row-major); positions outside the grid are zero-filled.
+template <typename HT>
+__device__ __forceinline__ void stage_strip(const HT* h, int nx, int ny, int xb, int yb, HT* S,
+                                            int lane) {
+  for (int i = lane; i < kStageRows * kStageCols; i += 32) {
+    const int r = i / kStageCols, col = i - r * kStageCols;
+    const int x = xb + col, y = yb + r;
+    const bool in = x >= 0 && x < nx && y >= 0 && y < ny;
+    cp_async_elem(S + i, in ? h + ((size_t)y * nx + x) : h, in);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+}
+
+// Donor mask from packed codes: byte 0 = row above, 1 = own row, 2 = row
+// below, of the left lane (cl), this lane (cw) and the right lane (cr).
+__device__ __forceinline__ int mask_from_packed(unsigned cl, unsigned cw, unsigned cr) {
+  const unsigned eL = __vcmpeq4(cl, 0xEE020407u);  // NW: 7, W: 4, SW: 2
+  const unsigned eC = __vcmpeq4(cw, 0xEE01EE06u);  // N: 6, S: 1
+  const unsigned eR = __vcmpeq4(cr, 0xEE000305u);  // NE: 5, E: 3, SE: 0
+  return (int)((eL & 1u) | ((eC & 1u) << 1) | ((eR & 1u) << 2) | (((eL >> 8) & 1u) << 3) |
+               (((eR >> 8) & 1u) << 4) | (((eL >> 16) & 1u) << 5) | (((eC >> 16) & 1u) << 6) |
+               (((eR >> 16) & 1u) << 7));
+}
+
+template <typename HT, typename CT>
+__device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
+  static_assert(kStageRows * kStageCols * sizeof(HT) <= kWarpBytes, "strip fits the warp slice");
+  constexpr int kAlign = 16 / (int)sizeof(HT);  // staged start: a 16-byte multiple
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int gw = blockIdx.x * kWarps + w, nw = (int)gridDim.x * kWarps;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  HT* S = reinterpret_cast<HT*>(dyn_smem + w * kWarpBytes);
+  const int nx = a.nx, ny = a.ny;
+  const int nsx = (nx + kStripOut - 1) / kStripOut;
+  const int units = nsx * ((ny + kStripRows - 1) / kStripRows);
+  for (int u = gw; u < units; u += nw) {
+    const int sy = u / nsx, sx = u - sy * nsx;
+    const int x0 = sx * kStripOut;  // first owned column
+    const int x = x0 - 1 + lane;    // this lane's column
+    const int y0 = sy * kStripRows, y1 = min(ny, y0 + kStripRows);
+    const bool xin = x >= 0 && x < nx;
+    const bool xperim = x == 0 || x == nx - 1;
+    const bool own = lane >= 1 && lane <= kStripOut && xin;
+    // staged column of this lane's cell: xb is x0 - 2 rounded down
+    const int xb = (x0 - 2) & ~(kAlign - 1), yb = y0 - 2;
+    const int sc = x - xb;  // 1..34
+    if (!a.frozen) stage_strip(a.h, nx, ny, xb, yb, S, lane);
+    HT ul = HT(0), uc = HT(0), ur = HT(0), ml = HT(0), mc = HT(0), mr = HT(0);
+    if (!a.frozen) {
+      ul = S[sc - 1];
+      uc = S[sc];
+      ur = S[sc + 1];
+      ml = S[kStageCols + sc - 1];
+      mc = S[kStageCols + sc];
+      mr = S[kStageCols + sc + 1];
+    }
+    unsigned cw = 0xFFFFFFFFu;  // codes of rows y-2, y-1, y in bytes 0, 1, 2
+    for (int y = y0 - 1; y <= y1; ++y) {
+      int cd = 0xFF;
+      const bool yin = y >= 0 && y < ny;
+      if (!a.frozen) {
+        const HT* Sd = S + (y + 1 - yb) * kStageCols + sc;
+        const HT dl = Sd[-1], dc = Sd[0], dr = Sd[1];
+        if (xin && yin) {
+          if (xperim || y == 0 || y == ny - 1) {
+            cd = kEdge;
+          } else {
+            const HT v[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
+            cd = receiver_from(mc, v);
+          }
+          if (own && y >= y0 && y < y1) a.code[(size_t)y * nx + x] = (uint8_t)cd;
+        }
+        ul = ml; uc = mc; ur = mr;
+        ml = dl; mc = dc; mr = dr;
+      } else if (xin && yin) {
+        cd = a.code[(size_t)y * nx + x];
+      }
+      cw = ((cw >> 8) & 0xFFFFu) | ((unsigned)cd << 16);
+      const unsigned cl = __shfl_up_sync(0xffffffffu, cw, 1);
+      const unsigned cr = __shfl_down_sync(0xffffffffu, cw, 1);
+      if (own && y - 1 >= y0 && y - 1 < y1)
+        a.mask[(size_t)(y - 1) * nx + x] = (uint8_t)mask_from_packed(cl, cw, cr);
+    }
+    __syncwarp();  // S is restaged by the next unit
+  }
+  trace_point(a.st, kTrLocal + 1);
+  if (!grid_barrier(a.st, gridDim.x)) return false;
+  trace_point(a.st, kTrCodes);
+  return true;
+}
+
+// Algs 1-2 and level 0 of Alg 3 (the stage calls and the device-wide form).
+// Returns false if a barrier was abandoned.
+template <typename HT, typename CT>
+__device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& s) {
   const unsigned G = gridDim.x;
   const int b = blockIdx.x, t = threadIdx.x, w = t >> 5, lane = t & 31;
   const int nx = a.nx, ny = a.ny, N = a.N;
-  // chunk and warp ranges start at multiples of 4 cells (128 per warp round)
-  const int chunk = ((N + (int)G - 1) / (int)G + 127) & ~127;
-  const int c0 = min(N, b * chunk), c1 = min(N, c0 + chunk);
-  const int wchunk = ((c1 - c0 + kWarps - 1) / kWarps + 127) & ~127;
-  const int w0 = min(c1, c0 + w * wchunk), w1 = min(c1, w0 + wchunk);
-  if (b == 0 && t == 0) a.st->private_overflow = 0;
-
+  int w0, w1;
+  warp_range(N, (int)G, b, w, &w0, &w1);
   // receiver codes and the count of cells without receiver, per warp
-  int wcnt = 0;
-  {
-    int x = w0 + lane, y = 0;
-    if (w0 < w1) {
-      y = x / nx;
-      x -= y * nx;
-    }
-    for (int base = w0; base < w1; base += 32) {
-      const int c = base + lane;
-      // the three rows two iterations ahead, into L1 (in-grid addresses only)
-      const int cp = c + 64;
-      if (!a.frozen && cp < w1 && cp > nx && cp + nx < N) {
-        prefetch_l1(a.h + (cp - nx));
-        prefetch_l1(a.h + cp);
-        prefetch_l1(a.h + (cp + nx));
-      }
-      int code = kEdge;
-      if (c < w1) {
-        if (!a.frozen) {
-          const bool perim = (x == 0 || y == 0 || x == nx - 1 || y == ny - 1);
-          code = perim ? kEdge : receiver_of(a.h, c, nx);
-          a.code[c] = (uint8_t)code;
-        } else {
-          code = a.code[c];
-        }
-      }
-      wcnt += __popc(__ballot_sync(0xffffffffu, c < w1 && no_receiver(code)));
-      x += 32;
-      while (x >= nx) {
-        x -= nx;
-        ++y;
-      }
-    }
-  }
+  const int wcnt = codes_sweep(a, w0, w1, lane);
   if (lane == 0) s.wcount[w] = wcnt;
   __syncthreads();
   if (t == 0) {
@@ -546,14 +691,7 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
   block_prefix_of_partials<kBD>(a.partial, (int)G, b, &prefix, &total, s.sum);
   int wpre = 0;
   for (int i = 0; i < w; ++i) wpre += s.wcount[i];
-  int mine = 0;
-  for (int i = 0; i < kWarps; ++i) mine += s.wcount[i];
-  *n0 = mine;
-  // donor masks and the cells without receiver, ascending, into the global
-  // level 0 and this block's private level 0
-  int* pq = a.pq + (size_t)b * a.pcap;
-  uint8_t* pqm = a.pqm + (size_t)b * a.pcap;
-  uint8_t* pqk = a.pqk + (size_t)b * a.pcap;
+  // donor masks, and the cells without receiver, ascending, as level 0
   {
     // Each lane takes 4 consecutive cells (w0 is a multiple of 4): their
     // masks are built as one 32-bit word, byte by byte in parallel.
@@ -588,13 +726,7 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         if ((f >> (8 * i)) & 1u) {
-          const int ci = c + i;
-          a.queue[prefix + pos] = ci;
-          if (pos < a.pcap) {
-            pq[pos] = ci;
-            pqm[pos] = (uint8_t)(mword >> (8 * i));
-            pqk[pos] = (uint8_t)(cword >> (8 * i));
-          }
+          a.queue[prefix + pos] = c + i;
           ++pos;
         }
       }
@@ -613,14 +745,17 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
 }
 
 // ---- phase: device-wide Alg 3 ----------------------------------------------------
-// Returns the number of levels L, or -1 if a barrier was abandoned or the
-// receiver graph left cells unreached (a cycle; recorded as kErrInval).
+
+// Level 0 is queue[0, hi0).  Returns the number of levels L, or -1 if a
+// barrier was abandoned or (check_all) the receiver graph left cells
+// unreached (a cycle; recorded as kErrInval).
 template <typename HT, typename CT>
-__device__ __noinline__ int phase_global_levels(const StepArgs<HT, CT>& a, Shared& s) {
+__device__ __noinline__ int phase_global_levels(const StepArgs<HT, CT>& a, Shared& s, int hi0,
+                                                bool check_all) {
   const unsigned G = gridDim.x;
   const int b = blockIdx.x, t = threadIdx.x;
   const int nx = a.nx;
-  int lo = 0, hi = a.levels[1], l = 0;
+  int lo = 0, hi = hi0, l = 0;
   while (true) {
     const int S = hi - lo;
     if (S <= kNarrow) {
@@ -718,7 +853,7 @@ __device__ __noinline__ int phase_global_levels(const StepArgs<HT, CT>& a, Share
   // L = l + 1 levels; every cell must have been reached
   const int L = l + 1;
   if (b == 0 && t == 0) a.st->nlevels = L;
-  if (a.levels[L] != a.N) {
+  if (check_all && a.levels[L] != a.N) {
     if (b == 0 && t == 0) set_error(a.st, kErrInval);
     return -1;
   }
@@ -822,12 +957,13 @@ __device__ __noinline__ bool phase_global_erode(const StepArgs<HT, CT>& a, int L
   return true;
 }
 
-// ---- phase: block-private Algs 3-6 -------------------------------------------------
-// Returns 1 if done privately, 0 if the step must fall back to the
-// device-wide form, -1 if a barrier was abandoned.
+// ---- block tier: Algs 3-6 on a block-private queue -----------------------------------
+// Level 0 is pq[0, n0) of this block's region, with the entries' donor masks
+// in pqm and receiver codes in pqk.  Returns the number of cells handled, or
+// -1 if the forest outgrows the region (pcap entries, kMaxPrivLevels levels);
+// then nothing was eroded.  Block barriers only.
 template <typename HT, typename CT>
-__device__ __noinline__ int phase_private(const StepArgs<HT, CT>& a, Shared& s, int n0) {
-  const unsigned G = gridDim.x;
+__device__ __noinline__ int private_forest(const StepArgs<HT, CT>& a, Shared& s, int n0) {
   const int b = blockIdx.x, t = threadIdx.x;
   const int nx = a.nx;
   int* pq = a.pq + (size_t)b * a.pcap;
@@ -965,11 +1101,7 @@ __device__ __noinline__ int phase_private(const StepArgs<HT, CT>& a, Shared& s, 
     lo = hi;
     hi = run;
   }
-  if (ovf && t == 0) a.st->private_overflow = 1;
-  trace_point(a.st, kTrLocal + 3);
-  if (!grid_barrier(a.st, G)) return -1;
-  trace_point(a.st, kTrPrivBfs);
-  if (ld_volatile(&a.st->private_overflow)) return 0;
+  if (ovf) return -1;
 
   // Alg 4 in queue order, this block's levels from the highest down to level
   // 1 (a time step needs the counts of eroding cells only): an entry's count
@@ -1039,43 +1171,67 @@ __device__ __noinline__ int phase_private(const StepArgs<HT, CT>& a, Shared& s, 
     }
     __syncthreads();
   }
-  trace_point(a.st, kTrPrivEro);
-  return 1;
+  return s.plev[PL];
 }
+
+}  // namespace lem
+
+#include "lem_tiles.cuh"
+
+namespace lem {
 
 template <typename HT, typename CT>
 __global__ void __launch_bounds__(kBD, 1) lem_step_kernel(StepArgs<HT, CT> a) {
   __shared__ Shared s;
-  const unsigned G = gridDim.x;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  if ((a.phases & kPhTiles) && lead) {
+    a.st->dev_roots[0] = a.st->dev_roots[1] = 0;
+    a.st->covered[0] = a.st->covered[1] = 0;
+  }
 
   for (int step = 0; step < a.nsteps; ++step) {
     trace_point(a.st, kTrStart + step);
-    int n0 = 0;
-    if (a.phases & kPhRec)
-      if (!phase_receivers(a, s, &n0)) return;
-
-    if (a.phases & kPhPrivate) {
-      const int r = phase_private(a, s, n0);
-      if (r < 0) return;
-      if (r == 0) {
-        const int L = phase_global_levels(a, s);
+    if (a.phases & kPhTiles) {
+      // the tiered step: Alg 1, a grid barrier, the warp and block tiers, a
+      // grid barrier, and the device tier only if some roots reached it
+      const int par = step & 1;
+      if (!phase_codes(a)) return;
+      if (lead) {
+        // every block has left the previous step, the last reader of these
+        a.st->dev_roots[par ^ 1] = 0;
+        a.st->covered[par ^ 1] = 0;
+      }
+      phase_tiles(a, s, &a.st->dev_roots[par], &a.st->covered[par]);
+      if (!grid_barrier(a.st, gridDim.x)) return;
+      trace_point(a.st, kTrTilesEnd);
+      const int dr = ld_volatile(&a.st->dev_roots[par]);
+      if (dr > 0) {
+        if (lead) {
+          a.levels[0] = 0;
+          a.levels[1] = dr;
+        }
+        const int L = phase_global_levels(a, s, dr, false);
         if (L < 0) return;
         if (!phase_global_accumulate(a, L)) return;
-        if (!phase_global_erode(a, L)) return;
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.st->global_steps += 1;
-      } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (!phase_global_erode(a, L)) return;  // ends with a grid barrier
+        if (lead) {
+          a.st->covered[par] += a.levels[L];
+          a.st->tier_cells[2] += (unsigned long long)a.levels[L];
+          a.st->global_steps += 1;
+        }
+      } else if (lead) {
         a.st->private_steps += 1;
       }
-      if (step + 1 < a.nsteps) {
-        if (!grid_barrier(a.st, G)) return;
-        trace_point(a.st, kTrStepEnd);
-      }
+      // every cell lies in exactly one tree unless a frozen graph has a cycle
+      if (lead && ld_volatile(&a.st->covered[par]) != a.N) set_error(a.st, kErrInval);
       continue;
     }
 
+    if (a.phases & kPhRec)
+      if (!phase_receivers(a, s)) return;
     int L = -1;
     if (a.phases & kPhLev) {
-      L = phase_global_levels(a, s);
+      L = phase_global_levels(a, s, a.levels[1], true);
       if (L < 0) return;
     }
     if (a.phases & (kPhAcc | kPhEro)) {

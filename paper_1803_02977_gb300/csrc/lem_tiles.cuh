@@ -1,0 +1,293 @@
+// lem_tiles.cuh -- Algs 3-6 of one time step on warp-private forests.
+//
+// Included by lem_step_kernel.cuh after the phase functions it builds on.
+//
+// The grid is cut into tiles of kTileW x kTileH cells.  A warp takes one
+// tile at a time and handles every tree rooted at one of the tile's cells
+// without receiver (level 0 of Alg 3): it grows their breadth-first levels
+// (Alg 3), pushes cell counts from the deepest level up (Alg 4) and erodes
+// from level 0 up (Algs 5-6), entirely in its own slice of shared memory and
+// with warp barriers only.  Trees are disjoint, so warps never touch the same
+// cell and need no synchronisation with one another -- the paper's private
+// queues ("Independent Parallelism", RB+PQ) at warp granularity, with the
+// queue held on chip.  The donor masks (Alg 2) come from the codes pass.
+//
+// A forest that outgrows the warp's slice (kCap entries or kTileLv levels)
+// is abandoned before anything is written; its tile goes to the block tier,
+// which runs the same trees on a block-private queue in global memory with
+// block barriers (private_forest).  A block whose tier outgrows its queue
+// share hands the roots to the device tier: device-wide levels after a grid
+// barrier (phase_global_levels and friends).  Every tier applies the same
+// per-cell arithmetic, so the elevations do not depend on which tier ran.
+#pragma once
+
+namespace lem {
+
+static_assert(2 * (kTileLv + 1) <= kTileLvBytes, "level offsets fit");
+
+// One warp's forest in shared memory.  Entry j: cell c[j], parent entry
+// p[j] (the entry of its receiver), receiver code d[j] (0..7 for levels >= 1,
+// 8 or 9 at level 0) and v[j], which holds the cell count (its first four
+// bytes) until the entry is eroded and the new elevation afterwards.
+template <typename HT>
+struct TileQ {
+  static constexpr int kEntryBytes = (int)sizeof(HT) + 4 + 2 + 1;
+  static constexpr int kCap = ((kWarpBytes - kTileLvBytes) / kEntryBytes) & ~31;
+  static_assert(kCap >= kTileW * kTileH, "a tile's level 0 always fits");
+  unsigned short* lev;
+  HT* v;
+  int* c;
+  unsigned short* p;
+  uint8_t* d;
+  __device__ __forceinline__ explicit TileQ(unsigned char* base) {
+    lev = reinterpret_cast<unsigned short*>(base);
+    v = reinterpret_cast<HT*>(base + kTileLvBytes);
+    c = reinterpret_cast<int*>(base + kTileLvBytes + sizeof(HT) * kCap);
+    p = reinterpret_cast<unsigned short*>(base + kTileLvBytes + (sizeof(HT) + 4) * kCap);
+    d = base + kTileLvBytes + (sizeof(HT) + 6) * kCap;
+  }
+  __device__ __forceinline__ unsigned* cnt(int j) const {
+    return reinterpret_cast<unsigned*>(v + j);
+  }
+};
+
+// Level 0 of one tile as seen by lane `lane`: the row codes of its column.
+// Out-of-grid positions read as 0 (a cell with a receiver: never a root).
+__device__ __forceinline__ void tile_codes(const uint8_t* code, int tile, int tiles_x, int nx,
+                                           int ny, int lane, int* cd, int* x, int* y0) {
+  const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+  *x = tx * kTileW + lane;
+  *y0 = ty * kTileH;
+#pragma unroll
+  for (int r = 0; r < kTileH; ++r) {
+    const int y = *y0 + r;
+    cd[r] = (*x < nx && y < ny) ? code[(size_t)y * nx + *x] : 0;
+  }
+}
+
+// Append the roots of `tile` to the device tier's level 0 (queue[0, n)).
+__device__ __forceinline__ void push_tile_roots_device(const uint8_t* code, int* queue,
+                                                       int* dev_roots, int tile, int tiles_x,
+                                                       int nx, int ny, int lane) {
+  int cd[kTileH], x, y0;
+  tile_codes(code, tile, tiles_x, nx, ny, lane, cd, &x, &y0);
+#pragma unroll
+  for (int r = 0; r < kTileH; ++r) {
+    const bool f = cd[r] >= kSink;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (bal == 0) continue;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(dev_roots, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (f) queue[base + __popc(bal & ((1u << lane) - 1u))] = (y0 + r) * nx + x;
+  }
+}
+
+// Algs 3-6 on the trees rooted in `tile`, by one warp.  Returns the number
+// of cells handled, or -1 if the forest does not fit (nothing was written).
+template <typename HT, typename CT>
+__device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const TileQ<HT>& q, int tile,
+                                           int lane) {
+  using Q = TileQ<HT>;
+  const int nx = a.nx, ny = a.ny;
+  const unsigned lt = (1u << lane) - 1u;
+  // level 0: the tile's cells without receiver, in row order
+  int n = 0;
+  {
+    int cd[kTileH], x, y0;
+    tile_codes(a.code, tile, a.tiles_x, nx, ny, lane, cd, &x, &y0);
+#pragma unroll
+    for (int r = 0; r < kTileH; ++r) {
+      const bool f = cd[r] >= kSink;
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (f) {
+        const int pos = n + __popc(bal & lt);
+        q.c[pos] = (y0 + r) * nx + x;
+        q.d[pos] = (uint8_t)cd[r];
+      }
+      n += __popc(bal);
+    }
+  }
+  if (lane == 0) {
+    q.lev[0] = 0;
+    q.lev[1] = (unsigned short)n;
+  }
+  // Alg 3: level l+1 = the donors of level l, each entry's donors emitted
+  // together in k order
+  int lo = 0, hi = n, L = 1;
+  while (lo < hi) {
+    int run = hi;
+    for (int base = lo; base < hi; base += 32) {
+      const int j = base + lane;
+      int c = 0, msk = 0;
+      if (j < hi) {
+        c = q.c[j];
+        msk = a.mask[c];
+      }
+      const int k = __popc(msk);
+      int incl = k;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int tot = __shfl_sync(0xffffffffu, incl, 31);
+      if (run + tot > Q::kCap) return -1;
+      int pos = run + incl - k;
+      while (msk) {
+        const int kk = __ffs(msk) - 1;
+        msk &= msk - 1;
+        q.c[pos] = c + nbr_off(kk, nx);
+        q.p[pos] = (unsigned short)j;
+        q.d[pos] = (uint8_t)(7 - kk);
+        *q.cnt(pos) = 1u;
+        ++pos;
+      }
+      run += tot;
+    }
+    __syncwarp();
+    if (run == hi) break;
+    if (L >= kTileLv) return -1;
+    ++L;
+    if (lane == 0) q.lev[L] = (unsigned short)run;
+    lo = hi;
+    hi = run;
+  }
+  __syncwarp();
+  // Alg 4: each entry adds its final count to its parent's, deepest level
+  // first; level 1 has no eroding parent to feed
+  for (int l = L - 1; l >= 2; --l) {
+    const int l0 = q.lev[l], l1 = q.lev[l + 1];
+    for (int j = l0 + lane; j < l1; j += 32) atomicAdd(q.cnt(q.p[j]), *q.cnt(j));
+    __syncwarp();
+  }
+  // Alg 5 on level 0: pits are uplifted, the perimeter stays
+  for (int j = lane; j < n; j += 32) {
+    const int c = q.c[j];
+    HT hc = a.h[c];
+    if (q.d[j] == kSink) {
+      if constexpr (sizeof(HT) == 8) {
+        hc = __dadd_rn(hc, uplift_dt(a, c));
+      } else {
+        hc = __fadd_rn(hc, uplift_dt_f(a, c));
+      }
+      a.h[c] = hc;
+    }
+    q.v[j] = hc;
+  }
+  __syncwarp();
+  // Alg 6 from level 1 up: the receiver's new elevation is the parent's v
+  for (int l = 1; l < L; ++l) {
+    const int l0 = q.lev[l], l1 = q.lev[l + 1];
+    for (int j = l0 + lane; j < l1; j += 32) {
+      const int c = q.c[j];
+      const int k = q.d[j];
+      const unsigned count = *q.cnt(j);
+      const HT hr = q.v[q.p[j]];
+      const HT hn = erode_value(a, c, k, (CT)count, a.h[c], hr);
+      a.h[c] = hn;
+      q.v[j] = hn;
+    }
+    __syncwarp();
+  }
+  return hi;
+}
+
+// The block tier: level 0 = the roots of this block's nov overflowed tiles
+// (s.ovf_tiles).  Returns the number of cells handled, or 0 after handing
+// the roots to the device tier when the block's queue cannot hold them.
+template <typename HT, typename CT>
+__device__ __noinline__ int block_tier(const StepArgs<HT, CT>& a, Shared& s, int nov,
+                                       int* dev_roots) {
+  const int b = blockIdx.x, t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int nx = a.nx, ny = a.ny;
+  int* pq = a.pq + (size_t)b * a.pcap;
+  uint8_t* pqm = a.pqm + (size_t)b * a.pcap;
+  uint8_t* pqk = a.pqk + (size_t)b * a.pcap;
+  for (int i = w; i < nov; i += kWarps) {
+    int cd[kTileH], x, y0;
+    tile_codes(a.code, s.ovf_tiles[i], a.tiles_x, nx, ny, lane, cd, &x, &y0);
+#pragma unroll
+    for (int r = 0; r < kTileH; ++r) {
+      const bool f = cd[r] >= kSink;
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (bal == 0) continue;
+      int base = 0;
+      if (lane == 0) base = atomicAdd(&s.n0, __popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      const int pos = base + __popc(bal & ((1u << lane) - 1u));
+      if (f && pos < a.pcap) {
+        const int c = (y0 + r) * nx + x;
+        pq[pos] = c;
+        pqk[pos] = (uint8_t)cd[r];
+        pqm[pos] = a.mask[c];
+      }
+    }
+  }
+  __syncthreads();
+  const int n0 = s.n0;
+  const int done = (n0 <= a.pcap) ? private_forest(a, s, n0) : -1;
+  if (done >= 0) return done;
+  for (int i = w; i < nov; i += kWarps)
+    push_tile_roots_device(a.code, a.queue, dev_roots, s.ovf_tiles[i], a.tiles_x, nx, ny, lane);
+  return 0;
+}
+
+// The warp tier and the block tier of one step, for this block's share of
+// tiles.  Roots that neither tier can hold are appended to the device tier's
+// level 0 (queue, counter *dev_roots).  The cells handled are added to
+// *covered and to the per-tier totals.
+template <typename HT, typename CT>
+__device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, int* dev_roots,
+                                         int* covered) {
+  const int G = (int)gridDim.x, b = blockIdx.x, t = threadIdx.x, w = t >> 5, lane = t & 31;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  const TileQ<HT> q(dyn_smem + w * kWarpBytes);
+  const int T = a.ntiles;
+  const int t0 = (int)((long long)T * b / G), t1 = (int)((long long)T * (b + 1) / G);
+  if (t == 0) {
+    s.tile_next = t0;
+    s.n_ovf = 0;
+    s.n0 = 0;
+  }
+  __syncthreads();
+  long long mine = 0;
+  while (true) {
+    int tile = 0;
+    if (lane == 0) tile = atomicAdd(&s.tile_next, 1);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= t1) break;
+    const int r = tile_forest(a, q, tile, lane);
+    if (r >= 0) {
+      mine += r;
+      continue;
+    }
+    int i = 0;
+    if (lane == 0) i = atomicAdd(&s.n_ovf, 1);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i < kOvfCap) {
+      if (lane == 0) s.ovf_tiles[i] = tile;
+    } else {
+      push_tile_roots_device(a.code, a.queue, dev_roots, tile, a.tiles_x, a.nx, a.ny, lane);
+    }
+  }
+  // per-warp totals (lane 0's count is the warp's)
+  if (lane == 0) s.wcount[w] = (int)mine;
+  __syncthreads();
+  trace_point(a.st, kTrLocal + 4);
+  long long by_warps = 0, by_block = 0;
+  if (t == 0)
+    for (int i = 0; i < kWarps; ++i) by_warps += s.wcount[i];
+
+  // block tier: the overflowed tiles' roots as level 0 of a private queue
+  const int nov = min(s.n_ovf, kOvfCap);
+  if (nov > 0) by_block = block_tier(a, s, nov, dev_roots);
+  trace_point(a.st, kTrLocal + 5);
+  if (t == 0) {
+    atomicAdd(covered, (int)(by_warps + by_block));
+    atomicAdd(&a.st->tier_cells[0], (unsigned long long)by_warps);
+    atomicAdd(&a.st->tier_cells[1], (unsigned long long)by_block);
+  }
+}
+
+}  // namespace lem

@@ -55,6 +55,7 @@ SIGNATURES = [
     ("lem_selftest_wait", _I, [_VP]),
     ("lem_set_step_mode", _I, [_VP, _I]),
     ("lem_step_stats", _I, [_VP, _I64P, _I64P]),
+    ("lem_tier_stats", _I, [_VP, _I64P]),
     ("lem_trace_enable", _I, [_VP, _I]),
     ("lem_trace_read", _I, [_VP, _VP, _VP, _I, ctypes.POINTER(_I)]),
     ("lem_adjoint", _I, [_VP, _VP, _VP, _I, _I, _VP, ctypes.POINTER(_D), _VP]),
@@ -75,7 +76,7 @@ LEM_NOALLOC_MAX_CELLS = 1 << 18
 TRACE_PHASES = {1: "start", 2: "receivers", 3: "level0", 4: "bfs_wide", 5: "bfs_narrow",
                 6: "acc_wide", 7: "acc_narrow", 8: "uplift", 9: "erode_wide",
                 10: "erode_narrow", 11: "private_levels", 12: "private_accumulate",
-                13: "private_erode", 14: "step_end", 15: "block0_done"}
+                13: "private_erode", 14: "step_end", 15: "block0_done", 16: "tiles_end"}
 
 
 def lib(build_if_missing: bool = True):
@@ -192,10 +193,17 @@ def lem_set_step_mode(ctx, mode):
 
 
 def lem_step_stats(ctx):
-    """(steps on block-private queues, steps on device-wide levels)."""
+    """(steps without device-wide levels, steps with them)."""
     p, g = ctypes.c_int64(0), ctypes.c_int64(0)
     _check(lib().lem_step_stats(ctx, ctypes.byref(p), ctypes.byref(g)), "lem_step_stats")
     return p.value, g.value
+
+
+def lem_tier_stats(ctx):
+    """Cells handled by (warp tiles, block queues, device-wide levels)."""
+    v = (ctypes.c_int64 * 3)()
+    _check(lib().lem_tier_stats(ctx, v), "lem_tier_stats")
+    return tuple(int(x) for x in v)
 
 
 def lem_adjoint(ctx, h0, lambda_T, nsteps, ckpt_every, dLdU, lambda_0=None):

@@ -174,15 +174,18 @@ def test_step_matches_oracle_per_step():
     m2.close()
 
 
+# (name, grid, which lem_step tiers must run; None: not pinned)
 STEP_CASES = [
-    ("noise_256", lambda: synth.noise_surface(256, 256, 1), "private"),
-    ("noise_tilt_700x500", lambda: synth.noise_surface(700, 500, 3, south_tilt=1e-4), "private"),
-    ("int_300x300", lambda: _int_grid(300, 300, 9, levels=12), "private"),
-    # one long chain per row (about 1500 private levels each)
-    ("tilted_1500x64", lambda: _tilted(1500, 64, 7, slope=0.2), "private"),
-    # a cone draining the whole grid to one outlet: that block's forest
-    # outgrows its private share and the step falls back to device-wide levels
-    ("cone_300x300", lambda: _cone(300, 300, 11), "fallback"),
+    ("noise_256", lambda: synth.noise_surface(256, 256, 1), "tiles"),
+    ("noise_tilt_700x500", lambda: synth.noise_surface(700, 500, 3, south_tilt=1e-4), "tiles"),
+    ("int_300x300", lambda: _int_grid(300, 300, 9, levels=12), None),
+    # one chain of ~300 cells per row, rooted on the west edge: too deep for a
+    # warp's tile, small enough for the block-private queue
+    ("tilted_300x64", lambda: _tilted(300, 64, 5, slope=0.2), "block"),
+    # chains of ~1500 cells (eight per edge tile): beyond the block's share too
+    ("tilted_1500x64", lambda: _tilted(1500, 64, 7, slope=0.2), "device"),
+    # a cone draining the whole grid to one outlet: one tree of ~90k cells
+    ("cone_300x300", lambda: _cone(300, 300, 11), "device"),
 ]
 
 
@@ -216,12 +219,18 @@ def test_step_modes_match_oracle_and_each_other(name, make, path):
             assert np.abs(got - want).max() <= REL64 * max(np.abs(want).max(), 1.0)
             cur = got
         priv, wide = lem.lem_step_stats(mdl.ctx)
+        tiers = lem.lem_tier_stats(mdl.ctx)
         if mode == 1:
-            assert (priv, wide) == (0, 0)  # device-wide mode does not use the private form
-        elif path == "private":
-            assert priv == 4 and wide == 0
+            # device-wide mode does not use the tiered form
+            assert (priv, wide) == (0, 0) and tiers == (0, 0, 0)
         else:
-            assert wide >= 1
+            assert sum(tiers) == 4 * h0.size  # every cell handled once per step
+            if path == "tiles":
+                assert tiers[1] == tiers[2] == 0 and (priv, wide) == (4, 0)
+            elif path == "block":
+                assert tiers[1] > 0 and tiers[2] == 0 and (priv, wide) == (4, 0)
+            elif path == "device":
+                assert tiers[2] > 0 and wide >= 1
         hs[mode] = h.cpu().numpy()
         mdl.close()
     # same per-cell arithmetic in both forms: identical elevations
@@ -279,6 +288,11 @@ def test_frozen_cycle_is_reported():
     mdl.set_receivers(torch.tensor(rec, device=dev))
     with pytest.raises(lem.LemError) as e:
         mdl.levels()
+    assert e.value.status == lem.LEM_EINVAL
+    # the tiered step reaches no cell of the cycle either
+    with pytest.raises(lem.LemError) as e:
+        mdl.step(1)
+        mdl.sync()
     assert e.value.status == lem.LEM_EINVAL
     bad = np.arange(nx * ny, dtype=np.int32)
     bad[2 * nx + 2] = 0  # not a neighbour
