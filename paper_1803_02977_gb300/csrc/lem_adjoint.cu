@@ -67,9 +67,7 @@ __global__ void __launch_bounds__(kABD) adjoint_step_kernel(AdjArgs a) {
   const unsigned G = gridDim.x;
   const int b = blockIdx.x, t = threadIdx.x;
   const int gtid = b * kABD + t, gstride = (int)G * kABD;
-  __shared__ long long s_unused[1];
   __shared__ double s_red[kABD / 32];
-  (void)s_unused;
   for (int c = gtid; c < a.N; c += gstride) a.mu[c] = a.lam[c];
   if (!grid_barrier(a.st, G)) return;
   // donors first: level L-2 down to 0 pulls from the level above
@@ -255,7 +253,13 @@ extern "C" LEM_API int lem_adjoint(lem_ctx* c, const double* dev_h0, const doubl
 done:
   cudaStreamSynchronize(c->stream);
   // back to the caller's binding; stages derived from scratch states are stale
-  c->h = saved_h;
+  if (saved_h) {
+    const int rb = lem_bind_elevation(c, saved_h, c->p.dtype);
+    if (rc == LEM_OK) rc = rb;
+  } else {
+    c->h = nullptr;
+    c->tmap_ok = false;
+  }
   if (!c->frozen) c->rec_valid = false;
   c->lev_valid = c->acc_valid = false;
   cudaFree(ck);

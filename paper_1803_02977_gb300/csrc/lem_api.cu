@@ -10,6 +10,8 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched at run time)
+
 #include "lem.h"
 #include "lem_context.cuh"
 #include "lem_step_kernel.cuh"
@@ -173,6 +175,8 @@ StepArgs<HT, CT> make_args(lem_ctx* c, int phases, int nsteps) {
   a.pcap = c->pcap;
   a.tiles_x = (c->p.nx + kTileW - 1) / kTileW;
   a.ntiles = a.tiles_x * ((c->p.ny + kTileH - 1) / kTileH);
+  a.has_tmap = c->tmap_ok ? 1 : 0;
+  a.tmap = c->tmap;
   a.Udt = c->p.U * c->p.dt;
   a.Udt_f = (float)(c->p.U * c->p.dt);
   a.phases = phases;
@@ -221,6 +225,52 @@ int read_status(lem_ctx* c, int* nlevels) {
 }
 
 bool is_finite(double v) { return std::isfinite(v); }
+
+// Encode the TMA descriptor of the bound elevations (2-D: nx x ny elements,
+// box kStageCols x kStageRows, zero fill outside) into c->tmap; every launch
+// passes it in its kernel parameter.  Leaves c->tmap_ok false -- the step kernel then
+// stages strips with per-element copies -- when TMA cannot describe h (row
+// pitch or base not a multiple of 16 bytes) or the driver lacks the encoder.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int encode_tmap(lem_ctx* c) {
+  c->tmap_ok = false;
+  if (!c->h) return LEM_OK;
+  const size_t esz = c->p.dtype == LEM_F64 ? 8 : 4;
+  const size_t pitch = (size_t)c->p.nx * esz;
+  if (pitch % 16 != 0 || ((uintptr_t)c->h) % 16 != 0) return LEM_OK;
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return LEM_OK;
+    }
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  CUtensorMap m;
+  std::memset(&m, 0, sizeof(m));
+  const cuuint64_t dims[2] = {(cuuint64_t)c->p.nx, (cuuint64_t)c->p.ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+  const cuuint32_t box[2] = {(cuuint32_t)kStageCols, (cuuint32_t)kStageRows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(&m, esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                            2, c->h, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return LEM_OK;
+  static_assert(sizeof(m) == sizeof(c->tmap), "descriptor size");
+  std::memcpy(&c->tmap, &m, sizeof(m));
+  c->tmap_ok = true;
+  return LEM_OK;
+}
 
 }  // namespace
 
@@ -366,6 +416,8 @@ int lem_set_stream(lem_ctx* c, void* stream) {
 int lem_bind_elevation(lem_ctx* c, void* dev_h, int dtype) {
   if (!c || !dev_h || dtype != c->p.dtype) return LEM_EINVAL;
   c->h = dev_h;
+  const int rc = encode_tmap(c);
+  if (rc != LEM_OK) return rc;
   if (!c->frozen) c->rec_valid = false;
   c->lev_valid = c->frozen && c->lev_valid;
   c->acc_valid = c->frozen && c->acc_valid;

@@ -38,4 +38,6 @@ struct lem_ctx {
   double Kdt = 0, dxd = 0, area_scale = 0;
   double wait_limit_s = 2.0;
   unsigned long long* trace = nullptr;  // device trace buffer (lem_trace_enable)
+  lem::TmaDesc tmap{};      // TMA descriptor of the bound h (host copy)
+  bool tmap_ok = false;     // tmap describes the bound h
 };

@@ -44,6 +44,12 @@
 
 namespace lem {
 
+// A TMA tensor descriptor (the driver's opaque 128-byte CUtensorMap), held
+// in the kernel parameter so that each launch carries its own copy.
+struct alignas(64) TmaDesc {
+  unsigned long long w[16];
+};
+
 template <typename HT, typename CT>
 struct StepArgs {
   int nx, ny, N;
@@ -66,6 +72,8 @@ struct StepArgs {
   CT* cntq;             // cell count of each private-queue entry (queue order)
   int pcap;             // entries per block in pq
   int tiles_x, ntiles;  // warp-tier tiles per row, in total
+  int has_tmap;         // tmap describes h (else strips are staged element-wise)
+  TmaDesc tmap;         // TMA descriptor of h: 2-D, kStageCols x kStageRows box
   CT* cnt;
   const double2* Ftab;  // {F, F/(1+F)} for counts < kTableN: [0,N) cardinal, [N,2N) diagonal
   const float* gtab;    // F/(1+F) rounded to float, same layout
@@ -87,14 +95,15 @@ constexpr int kMaxPrivLevels = 2048;  // level offsets a private queue may hold
 constexpr int kOvfCap = 256;       // tiles a block keeps for its block tier
 constexpr int kTileW = 32;         // warp-tier tile width: one column per lane
 constexpr int kTileH = 8;          // warp-tier tile height
-constexpr int kWarpBytes = 6144;   // shared memory per warp for its forest
+constexpr int kWarpBytes = 7040;   // shared memory per warp for its forest
 constexpr int kTileLv = 127;       // levels a warp forest may hold
 constexpr int kTileLvBytes = 256;  // its level offsets, u16 [0, kTileLv]
 // dynamic shared memory of the step kernel: the warps' forests, or (later in
 // the step) the block tier's staging buffer
-constexpr int kDynSmem = kWarps * kWarpBytes > kStage * (int)(sizeof(int) + 1)
-                             ? kWarps * kWarpBytes
-                             : kStage * (int)(sizeof(int) + 1);
+constexpr int kPlevOffset = kStage * (int)(sizeof(int) + 1);  // block tier: level offsets
+constexpr int kBlockTierBytes = kPlevOffset + (kMaxPrivLevels + 1) * (int)sizeof(int);
+constexpr int kDynSmem =
+    kWarps * kWarpBytes > kBlockTierBytes ? kWarps * kWarpBytes : kBlockTierBytes;
 
 // ---- Alg 1: receivers ----------------------------------------------------------
 
@@ -490,8 +499,8 @@ struct Shared {
   int wcount[kWarps];
   int chunk[kPItems * kWarps];  // per (slot, warp) donor totals, then offsets
   int chunk_total;
-  int plev[kMaxPrivLevels + 1];
   int tile_next, n_ovf, n0;     // warp tier: next tile; block tier: tiles, roots
+  int off[8];                   // address offset of neighbour k
   int ovf_tiles[kOvfCap];
 };
 static_assert(kPItems * kWarps == 8 * 32, "one warp scans the chunk totals 8 per lane");
@@ -587,6 +596,68 @@ __device__ __forceinline__ void stage_strip(const HT* h, int nx, int ny, int xb,
   __syncwarp();
 }
 
+// ---- TMA and mbarrier primitives (inline PTX, sm_90+) ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Order this thread's earlier generic accesses to shared memory before
+// later asynchronous-proxy (TMA) writes to it.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// 2-D tiled TMA load of the box at element coordinates (x, y) into dst,
+// completing on bar.  x * element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// Wait for phase `parity` of bar, bounded by the context's wait limit.
+// Returns false (with kErrTimeout recorded) if the limit ran out or another
+// block recorded an error.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, DevState* st) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  unsigned it = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++it & 255u) == 0) {
+      if (ld_volatile(&st->err) != 0) return false;
+      if (global_ns() - t0 > st->wait_limit_ns) {
+        set_error(st, kErrTimeout);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
 // Donor mask from packed codes: byte 0 = row above, 1 = own row, 2 = row
 // below, of the left lane (cl), this lane (cw) and the right lane (cr).
 __device__ __forceinline__ int mask_from_packed(unsigned cl, unsigned cw, unsigned cr) {
@@ -600,16 +671,28 @@ __device__ __forceinline__ int mask_from_packed(unsigned cl, unsigned cw, unsign
 
 template <typename HT, typename CT>
 __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
-  static_assert(kStageRows * kStageCols * sizeof(HT) <= kWarpBytes, "strip fits the warp slice");
+  static_assert(kStageRows * kStageCols * sizeof(HT) + 16 <= kWarpBytes,
+                "strip and barrier fit the warp slice");
   constexpr int kAlign = 16 / (int)sizeof(HT);  // staged start: a 16-byte multiple
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int gw = blockIdx.x * kWarps + w, nw = (int)gridDim.x * kWarps;
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
   HT* S = reinterpret_cast<HT*>(dyn_smem + w * kWarpBytes);
+  unsigned long long* bar =
+      reinterpret_cast<unsigned long long*>(dyn_smem + (w + 1) * kWarpBytes - 16);
   const int nx = a.nx, ny = a.ny;
   const int nsx = (nx + kStripOut - 1) / kStripOut;
   const int units = nsx * ((ny + kStripRows - 1) / kStripRows);
-  for (int u = gw; u < units; u += nw) {
+  // TMA staging: one box load per strip, issued by lane 0, completing on the
+  // warp's mbarrier (phase parity alternates per strip)
+  // (the box destination must be 128-byte aligned; a warp whose slice is
+  // not stages element-wise instead)
+  const bool tma = a.has_tmap && !a.frozen && (smem_u32(S) & 127u) == 0;
+  if (tma && lane == 0) mbar_init(bar, 1);
+  __syncwarp();
+  unsigned parity = 0;
+  bool ok = true;
+  for (int u = gw; ok && u < units; u += nw) {
     const int sy = u / nsx, sx = u - sy * nsx;
     const int x0 = sx * kStripOut;  // first owned column
     const int x = x0 - 1 + lane;    // this lane's column
@@ -620,7 +703,18 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
     // staged column of this lane's cell: xb is x0 - 2 rounded down
     const int xb = (x0 - 2) & ~(kAlign - 1), yb = y0 - 2;
     const int sc = x - xb;  // 1..34
-    if (!a.frozen) stage_strip(a.h, nx, ny, xb, yb, S, lane);
+    if (tma) {
+      if (lane == 0) {
+        fence_proxy_async_smem();  // the previous strip's reads of S come first
+        mbar_expect_tx(bar, (unsigned)(kStageRows * kStageCols * sizeof(HT)));
+        tma_load_2d(S, &a.tmap, xb, yb, bar);
+      }
+      ok = __all_sync(0xffffffffu, mbar_wait(bar, parity, a.st));
+      parity ^= 1u;
+      if (!ok) break;
+    } else if (!a.frozen) {
+      stage_strip(a.h, nx, ny, xb, yb, S, lane);
+    }
     HT ul = HT(0), uc = HT(0), ur = HT(0), ml = HT(0), mc = HT(0), mr = HT(0);
     if (!a.frozen) {
       ul = S[sc - 1];
@@ -659,6 +753,8 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
     }
     __syncwarp();  // S is restaged by the next unit
   }
+  __syncwarp();
+  if (tma && lane == 0 && ok) mbar_inval(bar);
   trace_point(a.st, kTrLocal + 1);
   if (!grid_barrier(a.st, gridDim.x)) return false;
   trace_point(a.st, kTrCodes);
@@ -970,17 +1066,18 @@ __device__ __noinline__ int private_forest(const StepArgs<HT, CT>& a, Shared& s,
   uint8_t* pqm = a.pqm + (size_t)b * a.pcap;
   uint8_t* pqk = a.pqk + (size_t)b * a.pcap;
   int* pqf = a.pqf + (size_t)b * a.pcap;
-  extern __shared__ unsigned char dyn_smem[];
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
   int* stage_q = reinterpret_cast<int*>(dyn_smem);
   uint8_t* stage_k = dyn_smem + sizeof(int) * kStage;
+  int* plev = reinterpret_cast<int*>(dyn_smem + kPlevOffset);  // level offsets
   // Alg 3 on this block's trees.  Each entry carries its donor mask and its
   // receiver code, written when it is emitted, so later levels and sweeps
   // read them in queue order instead of gathering them.
   bool ovf = n0 > a.pcap;
   int lo = 0, hi = n0, PL = 1;
   if (t == 0) {
-    s.plev[0] = 0;
-    s.plev[1] = n0;
+    plev[0] = 0;
+    plev[1] = n0;
   }
   while (!ovf && lo < hi) {
     int run = hi;
@@ -1097,7 +1194,7 @@ __device__ __noinline__ int private_forest(const StepArgs<HT, CT>& a, Shared& s,
       break;
     }
     ++PL;
-    if (t == 0) s.plev[PL] = run;
+    if (t == 0) plev[PL] = run;
     lo = hi;
     hi = run;
   }
@@ -1109,7 +1206,7 @@ __device__ __noinline__ int private_forest(const StepArgs<HT, CT>& a, Shared& s,
   // [pqf, pqf + number of donors) in the next level.
   CT* cntq = a.cntq + (size_t)b * a.pcap;
   for (int l = PL - 1; l >= 1; --l) {
-    const int l0 = s.plev[l], l1 = s.plev[l + 1];
+    const int l0 = plev[l], l1 = plev[l + 1];
     for (int base = l0 + t; base < l1; base += kItems * kBD) {
       int fs[kItems], ns[kItems];
 #pragma unroll
@@ -1135,7 +1232,7 @@ __device__ __noinline__ int private_forest(const StepArgs<HT, CT>& a, Shared& s,
   }
   trace_point(a.st, kTrPrivAcc);
   // Alg 5 on level 0 (pits only), then Alg 6 from level 1 up
-  for (int j = t; j < s.plev[1]; j += kBD)
+  for (int j = t; j < plev[1]; j += kBD)
     if (pqk[j] == kSink) {
       const int c = pq[j];
       if constexpr (sizeof(HT) == 8) {
@@ -1146,7 +1243,7 @@ __device__ __noinline__ int private_forest(const StepArgs<HT, CT>& a, Shared& s,
     }
   __syncthreads();
   for (int l = 1; l < PL; ++l) {
-    const int l0 = s.plev[l], l1 = s.plev[l + 1];
+    const int l0 = plev[l], l1 = plev[l + 1];
     for (int base = l0 + t; base < l1; base += kItems * kBD) {
       int cs[kItems], ks[kItems];
       CT ns[kItems];
@@ -1171,7 +1268,7 @@ __device__ __noinline__ int private_forest(const StepArgs<HT, CT>& a, Shared& s,
     }
     __syncthreads();
   }
-  return s.plev[PL];
+  return plev[PL];
 }
 
 }  // namespace lem
@@ -1181,7 +1278,7 @@ __device__ __noinline__ int private_forest(const StepArgs<HT, CT>& a, Shared& s,
 namespace lem {
 
 template <typename HT, typename CT>
-__global__ void __launch_bounds__(kBD, 1) lem_step_kernel(StepArgs<HT, CT> a) {
+__global__ void __launch_bounds__(kBD, 1) lem_step_kernel(const __grid_constant__ StepArgs<HT, CT> a) {
   __shared__ Shared s;
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   if ((a.phases & kPhTiles) && lead) {

@@ -25,26 +25,27 @@ namespace lem {
 
 static_assert(2 * (kTileLv + 1) <= kTileLvBytes, "level offsets fit");
 
-// One warp's forest in shared memory.  Entry j: cell c[j], parent entry
-// p[j] (the entry of its receiver), receiver code d[j] (0..7 for levels >= 1,
-// 8 or 9 at level 0) and v[j], which holds the cell count (its first four
-// bytes) until the entry is eroded and the new elevation afterwards.
+// One warp's forest in shared memory.  Entry j: cell c[j]; pd[j] = parent
+// entry (the entry of its receiver) << 4 | receiver code (0..7 for levels
+// >= 1, 8 or 9 at level 0); v[j] holds the cell count (its first four bytes)
+// until the entry is eroded and the new elevation afterwards.
 template <typename HT>
 struct TileQ {
-  static constexpr int kEntryBytes = (int)sizeof(HT) + 4 + 2 + 1;
-  static constexpr int kCap = ((kWarpBytes - kTileLvBytes) / kEntryBytes) & ~31;
+  static constexpr int kHead = kTileLvBytes;
+  static constexpr int kEntryBytes = (int)sizeof(HT) + 4 + 4;
+  static constexpr int kCap = ((kWarpBytes - kHead) / kEntryBytes) & ~7;
   static_assert(kCap >= kTileW * kTileH, "a tile's level 0 always fits");
+  static_assert(kCap < (1 << 27), "parent index fits pd");
+  static_assert(kHead % 16 == 0, "entry arrays stay aligned");
   unsigned short* lev;
   HT* v;
   int* c;
-  unsigned short* p;
-  uint8_t* d;
+  unsigned* pd;
   __device__ __forceinline__ explicit TileQ(unsigned char* base) {
     lev = reinterpret_cast<unsigned short*>(base);
-    v = reinterpret_cast<HT*>(base + kTileLvBytes);
-    c = reinterpret_cast<int*>(base + kTileLvBytes + sizeof(HT) * kCap);
-    p = reinterpret_cast<unsigned short*>(base + kTileLvBytes + (sizeof(HT) + 4) * kCap);
-    d = base + kTileLvBytes + (sizeof(HT) + 6) * kCap;
+    v = reinterpret_cast<HT*>(base + kHead);
+    c = reinterpret_cast<int*>(base + kHead + sizeof(HT) * kCap);
+    pd = reinterpret_cast<unsigned*>(base + kHead + (sizeof(HT) + 4) * kCap);
   }
   __device__ __forceinline__ unsigned* cnt(int j) const {
     return reinterpret_cast<unsigned*>(v + j);
@@ -83,19 +84,27 @@ __device__ __forceinline__ void push_tile_roots_device(const uint8_t* code, int*
   }
 }
 
-// Algs 3-6 on the trees rooted in `tile`, by one warp.  Returns the number
-// of cells handled, or -1 if the forest does not fit (nothing was written).
+// Algs 3-6 on the trees rooted in `tile`, by one warp.  off[k] is the
+// address offset of neighbour k.  Returns the number of cells handled, or -1
+// if the forest does not fit (nothing was written).
 template <typename HT, typename CT>
-__device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const TileQ<HT>& q, int tile,
-                                           int lane) {
+__device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const TileQ<HT>& q,
+                                           const int* off, int tile, int lane) {
   using Q = TileQ<HT>;
   const int nx = a.nx, ny = a.ny;
   const unsigned lt = (1u << lane) - 1u;
+  const uint8_t* mask = a.mask;
   // level 0: the tile's cells without receiver, in row order
   int n = 0;
   {
-    int cd[kTileH], x, y0;
-    tile_codes(a.code, tile, a.tiles_x, nx, ny, lane, cd, &x, &y0);
+    const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
+    const int x = tx * kTileW + lane, y0 = ty * kTileH;
+    int cd[kTileH];
+#pragma unroll
+    for (int r = 0; r < kTileH; ++r) {
+      const int y = y0 + r;
+      cd[r] = (x < nx && y < ny) ? a.code[(size_t)y * nx + x] : 0;
+    }
 #pragma unroll
     for (int r = 0; r < kTileH; ++r) {
       const bool f = cd[r] >= kSink;
@@ -103,7 +112,7 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
       if (f) {
         const int pos = n + __popc(bal & lt);
         q.c[pos] = (y0 + r) * nx + x;
-        q.d[pos] = (uint8_t)cd[r];
+        q.pd[pos] = (unsigned)cd[r];
       }
       n += __popc(bal);
     }
@@ -112,60 +121,77 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
     q.lev[0] = 0;
     q.lev[1] = (unsigned short)n;
   }
-  // Alg 3: level l+1 = the donors of level l, each entry's donors emitted
-  // together in k order
-  int lo = 0, hi = n, L = 1;
-  while (lo < hi) {
-    int run = hi;
-    for (int base = lo; base < hi; base += 32) {
-      const int j = base + lane;
-      int c = 0, msk = 0;
-      if (j < hi) {
-        c = q.c[j];
-        msk = a.mask[c];
-      }
-      const int k = __popc(msk);
-      int incl = k;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const int tot = __shfl_sync(0xffffffffu, incl, 31);
-      if (run + tot > Q::kCap) return -1;
-      int pos = run + incl - k;
-      while (msk) {
-        const int kk = __ffs(msk) - 1;
-        msk &= msk - 1;
-        q.c[pos] = c + nbr_off(kk, nx);
-        q.p[pos] = (unsigned short)j;
-        q.d[pos] = (uint8_t)(7 - kk);
-        *q.cnt(pos) = 1u;
-        ++pos;
-      }
-      run += tot;
-    }
-    __syncwarp();
-    if (run == hi) break;
-    if (L >= kTileLv) return -1;
-    ++L;
-    if (lane == 0) q.lev[L] = (unsigned short)run;
-    lo = hi;
-    hi = run;
-  }
   __syncwarp();
+  // Alg 3 as one first-in first-out sweep: each window takes the next 32
+  // entries, whatever their levels, and appends their donors (k order per
+  // entry, entries in queue order), so the queue stays in level order.  The
+  // window that holds the first entry of level L ends level L+1's
+  // predecessors: level L+1 starts after the donors of the entries before it.
+  int head = 0, tail = n, L = 1, B = n;  // B: first entry of level L
+  while (head < tail) {
+    const int w = min(32, tail - head);
+    const int j = head + lane;
+    int c = 0, msk = 0;
+    if (lane < w) {
+      c = q.c[j];
+      msk = mask[c];
+    }
+    const int k = __popc(msk);
+    int incl = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    if (tail + tot > Q::kCap) return -1;
+    if (B >= head && B < head + w) {
+      const int before = B - head;  // lanes of level L-1 in this window
+      const int sb = __shfl_sync(0xffffffffu, incl, before > 0 ? before - 1 : 0);
+      if (L >= kTileLv) return -1;
+      ++L;
+      B = tail + (before > 0 ? sb : 0);
+      if (lane == 0) q.lev[L] = (unsigned short)B;
+    }
+    // the window's tot donors, one per lane: donor e belongs to the first
+    // lane s whose inclusive count exceeds e, as its (e - excl(s))-th bit
+    for (int e0 = 0; e0 < tot; e0 += 32) {
+      const int e = e0 + lane;
+      int s = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int v = __shfl_sync(0xffffffffu, incl, s + step - 1);
+        if (v <= e) s += step;
+      }
+      int pm = __shfl_sync(0xffffffffu, msk, s);
+      const int pc = __shfl_sync(0xffffffffu, c, s);
+      const int pex = __shfl_sync(0xffffffffu, incl - k, s);
+      if (e < tot) {
+        for (int r = e - pex; r > 0; --r) pm &= pm - 1;
+        const int kk = __ffs(pm) - 1;
+        const int pos = tail + e;
+        q.c[pos] = pc + off[kk];
+        q.pd[pos] = ((unsigned)(head + s) << 4) | (unsigned)(7 - kk);
+        *q.cnt(pos) = 1u;
+      }
+    }
+    tail += tot;
+    head += w;
+    __syncwarp();
+  }
+  // levels 0 .. L-1; q.lev[L] == tail
   // Alg 4: each entry adds its final count to its parent's, deepest level
   // first; level 1 has no eroding parent to feed
   for (int l = L - 1; l >= 2; --l) {
     const int l0 = q.lev[l], l1 = q.lev[l + 1];
-    for (int j = l0 + lane; j < l1; j += 32) atomicAdd(q.cnt(q.p[j]), *q.cnt(j));
+    for (int jj = l0 + lane; jj < l1; jj += 32) atomicAdd(q.cnt(q.pd[jj] >> 4), *q.cnt(jj));
     __syncwarp();
   }
   // Alg 5 on level 0: pits are uplifted, the perimeter stays
-  for (int j = lane; j < n; j += 32) {
-    const int c = q.c[j];
+  for (int jj = lane; jj < n; jj += 32) {
+    const int c = q.c[jj];
     HT hc = a.h[c];
-    if (q.d[j] == kSink) {
+    if ((q.pd[jj] & 15u) == (unsigned)kSink) {
       if constexpr (sizeof(HT) == 8) {
         hc = __dadd_rn(hc, uplift_dt(a, c));
       } else {
@@ -173,24 +199,23 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
       }
       a.h[c] = hc;
     }
-    q.v[j] = hc;
+    q.v[jj] = hc;
   }
   __syncwarp();
   // Alg 6 from level 1 up: the receiver's new elevation is the parent's v
   for (int l = 1; l < L; ++l) {
     const int l0 = q.lev[l], l1 = q.lev[l + 1];
-    for (int j = l0 + lane; j < l1; j += 32) {
-      const int c = q.c[j];
-      const int k = q.d[j];
-      const unsigned count = *q.cnt(j);
-      const HT hr = q.v[q.p[j]];
-      const HT hn = erode_value(a, c, k, (CT)count, a.h[c], hr);
+    for (int jj = l0 + lane; jj < l1; jj += 32) {
+      const int c = q.c[jj];
+      const unsigned pd = q.pd[jj];
+      const unsigned count = *q.cnt(jj);
+      const HT hn = erode_value(a, c, (int)(pd & 15u), (CT)count, a.h[c], q.v[pd >> 4]);
       a.h[c] = hn;
-      q.v[j] = hn;
+      q.v[jj] = hn;
     }
     __syncwarp();
   }
-  return hi;
+  return tail;
 }
 
 // The block tier: level 0 = the roots of this block's nov overflowed tiles
@@ -241,7 +266,7 @@ template <typename HT, typename CT>
 __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, int* dev_roots,
                                          int* covered) {
   const int G = (int)gridDim.x, b = blockIdx.x, t = threadIdx.x, w = t >> 5, lane = t & 31;
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
   const TileQ<HT> q(dyn_smem + w * kWarpBytes);
   const int T = a.ntiles;
   const int t0 = (int)((long long)T * b / G), t1 = (int)((long long)T * (b + 1) / G);
@@ -250,6 +275,7 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
     s.n_ovf = 0;
     s.n0 = 0;
   }
+  if (t < 8) s.off[t] = nbr_off(t, a.nx);
   __syncthreads();
   long long mine = 0;
   while (true) {
@@ -257,7 +283,7 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
     if (lane == 0) tile = atomicAdd(&s.tile_next, 1);
     tile = __shfl_sync(0xffffffffu, tile, 0);
     if (tile >= t1) break;
-    const int r = tile_forest(a, q, tile, lane);
+    const int r = tile_forest(a, q, s.off, tile, lane);
     if (r >= 0) {
       mine += r;
       continue;
