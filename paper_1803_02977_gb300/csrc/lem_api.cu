@@ -218,6 +218,7 @@ int read_status(lem_ctx* c, int* nlevels) {
     // an abandoned barrier may have left arrivals counted: start clean
     LEM_CUDA(cudaMemsetAsync(&c->st->bar_count, 0, sizeof(unsigned), c->stream));
     LEM_CUDA(cudaMemsetAsync(&c->st->err, 0, sizeof(int), c->stream));
+    LEM_CUDA(cudaMemsetAsync(c->st->tiles_next, 0, sizeof(c->st->tiles_next), c->stream));
     LEM_CUDA(cudaStreamSynchronize(c->stream));
     return err;
   }

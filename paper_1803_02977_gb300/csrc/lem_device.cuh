@@ -65,6 +65,7 @@ struct DevState {
   // roots handed to the device tier, cells handled by all tiers
   int dev_roots[2];
   int covered[2];
+  int tiles_next[2];  // warp-tier tiles claimed (zero between launches)
   unsigned long long tier_cells[3];  // cells handled by warp, block, device tier
 };
 

@@ -499,7 +499,7 @@ struct Shared {
   int wcount[kWarps];
   int chunk[kPItems * kWarps];  // per (slot, warp) donor totals, then offsets
   int chunk_total;
-  int tile_next, n_ovf, n0;     // warp tier: next tile; block tier: tiles, roots
+  int n_ovf, n0;                // block tier: overflowed tiles, roots
   int off[8];                   // address offset of neighbour k
   int ovf_tiles[kOvfCap];
 };
@@ -1298,9 +1298,10 @@ __global__ void __launch_bounds__(kBD, 1) lem_step_kernel(const __grid_constant_
         a.st->dev_roots[par ^ 1] = 0;
         a.st->covered[par ^ 1] = 0;
       }
-      phase_tiles(a, s, &a.st->dev_roots[par], &a.st->covered[par]);
+      phase_tiles(a, s, &a.st->tiles_next[par], &a.st->dev_roots[par], &a.st->covered[par]);
       if (!grid_barrier(a.st, gridDim.x)) return;
       trace_point(a.st, kTrTilesEnd);
+      if (lead) a.st->tiles_next[par] = 0;  // every block has stopped claiming
       const int dr = ld_volatile(&a.st->dev_roots[par]);
       if (dr > 0) {
         if (lead) {

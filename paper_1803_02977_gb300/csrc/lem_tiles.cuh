@@ -25,17 +25,18 @@ namespace lem {
 
 static_assert(2 * (kTileLv + 1) <= kTileLvBytes, "level offsets fit");
 
-// One warp's forest in shared memory.  Entry j: cell c[j]; pd[j] = parent
-// entry (the entry of its receiver) << 4 | receiver code (0..7 for levels
-// >= 1, 8 or 9 at level 0); v[j] holds the cell count (its first four bytes)
-// until the entry is eroded and the new elevation afterwards.
+// One warp's forest in shared memory.  Entry j: cell c[j]; the word pd[j]
+// = cell count << 16 | parent entry (the entry of its receiver) << 4 |
+// receiver code (0..7 for levels >= 1, 8 or 9 at level 0); and v[j], the
+// cell's elevation, copied in asynchronously when the entry is created and
+// replaced by the new elevation when the entry is eroded.
 template <typename HT>
 struct TileQ {
   static constexpr int kHead = kTileLvBytes;
   static constexpr int kEntryBytes = (int)sizeof(HT) + 4 + 4;
   static constexpr int kCap = ((kWarpBytes - kHead) / kEntryBytes) & ~7;
   static_assert(kCap >= kTileW * kTileH, "a tile's level 0 always fits");
-  static_assert(kCap < (1 << 27), "parent index fits pd");
+  static_assert(kCap < (1 << 12), "parent index and count fit pd");
   static_assert(kHead % 16 == 0, "entry arrays stay aligned");
   unsigned short* lev;
   HT* v;
@@ -47,10 +48,11 @@ struct TileQ {
     c = reinterpret_cast<int*>(base + kHead + sizeof(HT) * kCap);
     pd = reinterpret_cast<unsigned*>(base + kHead + (sizeof(HT) + 4) * kCap);
   }
-  __device__ __forceinline__ unsigned* cnt(int j) const {
-    return reinterpret_cast<unsigned*>(v + j);
-  }
 };
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
 
 // Level 0 of one tile as seen by lane `lane`: the row codes of its column.
 // Out-of-grid positions read as 0 (a cell with a receiver: never a root).
@@ -111,8 +113,10 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
       const unsigned bal = __ballot_sync(0xffffffffu, f);
       if (f) {
         const int pos = n + __popc(bal & lt);
-        q.c[pos] = (y0 + r) * nx + x;
+        const int c = (y0 + r) * nx + x;
+        q.c[pos] = c;
         q.pd[pos] = (unsigned)cd[r];
+        cp_async_elem(q.v + pos, a.h + c, true);
       }
       n += __popc(bal);
     }
@@ -144,11 +148,17 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
       if (lane >= o) incl += y;
     }
     const int tot = __shfl_sync(0xffffffffu, incl, 31);
-    if (tail + tot > Q::kCap) return -1;
+    if (tail + tot > Q::kCap) {
+      cp_async_wait_all();  // no copy may land in the slice after we leave
+      return -1;
+    }
     if (B >= head && B < head + w) {
       const int before = B - head;  // lanes of level L-1 in this window
       const int sb = __shfl_sync(0xffffffffu, incl, before > 0 ? before - 1 : 0);
-      if (L >= kTileLv) return -1;
+      if (L >= kTileLv) {
+        cp_async_wait_all();
+        return -1;
+      }
       ++L;
       B = tail + (before > 0 ? sb : 0);
       if (lane == 0) q.lev[L] = (unsigned short)B;
@@ -170,9 +180,10 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
         for (int r = e - pex; r > 0; --r) pm &= pm - 1;
         const int kk = __ffs(pm) - 1;
         const int pos = tail + e;
-        q.c[pos] = pc + off[kk];
-        q.pd[pos] = ((unsigned)(head + s) << 4) | (unsigned)(7 - kk);
-        *q.cnt(pos) = 1u;
+        const int cc = pc + off[kk];
+        q.c[pos] = cc;
+        q.pd[pos] = (1u << 16) | ((unsigned)(head + s) << 4) | (unsigned)(7 - kk);
+        cp_async_elem(q.v + pos, a.h + cc, true);
       }
     }
     tail += tot;
@@ -184,22 +195,27 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
   // first; level 1 has no eroding parent to feed
   for (int l = L - 1; l >= 2; --l) {
     const int l0 = q.lev[l], l1 = q.lev[l + 1];
-    for (int jj = l0 + lane; jj < l1; jj += 32) atomicAdd(q.cnt(q.pd[jj] >> 4), *q.cnt(jj));
+    for (int jj = l0 + lane; jj < l1; jj += 32) {
+      const unsigned w = q.pd[jj];
+      atomicAdd(&q.pd[(w >> 4) & 0xFFFu], w & 0xFFFF0000u);
+    }
     __syncwarp();
   }
+  cp_async_wait_all();  // every entry's elevation has arrived
+  __syncwarp();
   // Alg 5 on level 0: pits are uplifted, the perimeter stays
   for (int jj = lane; jj < n; jj += 32) {
-    const int c = q.c[jj];
-    HT hc = a.h[c];
+    HT hc = q.v[jj];
     if ((q.pd[jj] & 15u) == (unsigned)kSink) {
+      const int c = q.c[jj];
       if constexpr (sizeof(HT) == 8) {
         hc = __dadd_rn(hc, uplift_dt(a, c));
       } else {
         hc = __fadd_rn(hc, uplift_dt_f(a, c));
       }
       a.h[c] = hc;
+      q.v[jj] = hc;
     }
-    q.v[jj] = hc;
   }
   __syncwarp();
   // Alg 6 from level 1 up: the receiver's new elevation is the parent's v
@@ -208,8 +224,8 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
     for (int jj = l0 + lane; jj < l1; jj += 32) {
       const int c = q.c[jj];
       const unsigned pd = q.pd[jj];
-      const unsigned count = *q.cnt(jj);
-      const HT hn = erode_value(a, c, (int)(pd & 15u), (CT)count, a.h[c], q.v[pd >> 4]);
+      const HT hn = erode_value(a, c, (int)(pd & 15u), (CT)(pd >> 16), q.v[jj],
+                                q.v[(pd >> 4) & 0xFFFu]);
       a.h[c] = hn;
       q.v[jj] = hn;
     }
@@ -263,27 +279,30 @@ __device__ __noinline__ int block_tier(const StepArgs<HT, CT>& a, Shared& s, int
 // level 0 (queue, counter *dev_roots).  The cells handled are added to
 // *covered and to the per-tier totals.
 template <typename HT, typename CT>
-__device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, int* dev_roots,
-                                         int* covered) {
-  const int G = (int)gridDim.x, b = blockIdx.x, t = threadIdx.x, w = t >> 5, lane = t & 31;
+__device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, int* tiles_next,
+                                         int* dev_roots, int* covered) {
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   const TileQ<HT> q(dyn_smem + w * kWarpBytes);
   const int T = a.ntiles;
-  const int t0 = (int)((long long)T * b / G), t1 = (int)((long long)T * (b + 1) / G);
   if (t == 0) {
-    s.tile_next = t0;
     s.n_ovf = 0;
     s.n0 = 0;
   }
   if (t < 8) s.off[t] = nbr_off(t, a.nx);
   __syncthreads();
   long long mine = 0;
-  while (true) {
-    int tile = 0;
-    if (lane == 0) tile = atomicAdd(&s.tile_next, 1);
-    tile = __shfl_sync(0xffffffffu, tile, 0);
-    if (tile >= t1) break;
+  // tiles are claimed one at a time from a device-wide counter; the next
+  // claim is issued before the current tile is processed
+  int tile = 0;
+  if (lane == 0) tile = atomicAdd(tiles_next, 1);
+  tile = __shfl_sync(0xffffffffu, tile, 0);
+  while (tile < T) {
+    int next = 0;
+    if (lane == 0) next = atomicAdd(tiles_next, 1);
     const int r = tile_forest(a, q, s.off, tile, lane);
+    const int cur = tile;
+    tile = __shfl_sync(0xffffffffu, next, 0);
     if (r >= 0) {
       mine += r;
       continue;
@@ -292,9 +311,9 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
     if (lane == 0) i = atomicAdd(&s.n_ovf, 1);
     i = __shfl_sync(0xffffffffu, i, 0);
     if (i < kOvfCap) {
-      if (lane == 0) s.ovf_tiles[i] = tile;
+      if (lane == 0) s.ovf_tiles[i] = cur;
     } else {
-      push_tile_roots_device(a.code, a.queue, dev_roots, tile, a.tiles_x, a.nx, a.ny, lane);
+      push_tile_roots_device(a.code, a.queue, dev_roots, cur, a.tiles_x, a.nx, a.ny, lane);
     }
   }
   // per-warp totals (lane 0's count is the warp's)

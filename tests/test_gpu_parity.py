@@ -180,13 +180,27 @@ STEP_CASES = [
     ("noise_tilt_700x500", lambda: synth.noise_surface(700, 500, 3, south_tilt=1e-4), "tiles"),
     ("int_300x300", lambda: _int_grid(300, 300, 9, levels=12), None),
     # one chain of ~300 cells per row, rooted on the west edge: too deep for a
-    # warp's tile, small enough for the block-private queue
-    ("tilted_300x64", lambda: _tilted(300, 64, 5, slope=0.2), "block"),
+    # warp's tile; the block or the device tier takes them, depending on how
+    # many edge tiles one block claims
+    ("tilted_300x64", lambda: _tilted(300, 64, 5, slope=0.2), None),
+    # one basin of ~700 cells around a single pit: larger than a warp's queue,
+    # within one block's, whichever block claims its tile
+    ("funnel_256", lambda: _funnel(256, 256, 13), "block"),
     # chains of ~1500 cells (eight per edge tile): beyond the block's share too
     ("tilted_1500x64", lambda: _tilted(1500, 64, 7, slope=0.2), "device"),
     # a cone draining the whole grid to one outlet: one tree of ~90k cells
     ("cone_300x300", lambda: _cone(300, 300, 11), "device"),
 ]
+
+
+def _funnel(nx, ny, seed, cx=48, cy=44, r=15.0):
+    h = 100.0 + synth.uniform01(seed, nx * ny).reshape(ny, nx)
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    d = np.hypot(x - cx, y - cy)
+    inside = d <= r
+    h[inside] = 50.0 + d[inside] + 0.001 * h[inside]
+    h[0, :] = h[-1, :] = h[:, 0] = h[:, -1] = 0.0
+    return h
 
 
 def _cone(nx, ny, seed):
