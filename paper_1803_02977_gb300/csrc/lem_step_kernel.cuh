@@ -174,10 +174,69 @@ __device__ __forceinline__ bool no_rounding_merge(typename Bits<HT>::U m, typena
 // group winners' slopes are evaluated in FP64 -- after checking that no other
 // neighbour of the group could round to the same slope.  Cells where that
 // check, or non-negative finiteness, fails take the reference form.
+// FP64 elevations, first try: the same decision from the high 32-bit words
+// of the values (sign, exponent, 20 mantissa bits), which order non-negative
+// doubles like the values themselves.  A group's minimum is exact when its
+// high word is unique in the group; no other member can round to the same
+// slope when none has the next high word (then it lies more than 2^32 of the
+// minimum's ulps above it) and the minimum lies at most 18 binades below h_c
+// (so the 2^32 ulps between consecutive high words exceed 4 ulps of h_c).  The two candidates' slopes
+// are compared in FP32 from the high words (relative error below 2^-19
+// each), deciding when they differ by more than 2^-16 of h_c plus 2^-16 of
+// the slopes.  Returns -1 when any of this does not hold.
+__device__ __forceinline__ int receiver_code_hi(const double hcd, const double* v) {
+  const unsigned hc = (unsigned)__double2hiint(hcd);
+  unsigned x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = (unsigned)__double2hiint(v[k]);
+  unsigned worst = hc;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) worst = max(worst, x[k]);
+  // non-negative, finite, and h_c (and anything within 18 binades below it)
+  // within the float exponent range
+  if (worst >= 0x7FF00000u || hc < (915u << 20) || hc >= (1151u << 20)) return -1;
+  const unsigned mC = min(min(x[1], x[3]), min(x[4], x[6]));
+  const unsigned mD = min(min(x[0], x[2]), min(x[5], x[7]));
+  if (mC == hc || mD == hc) return -1;
+  const bool hasC = mC < hc, hasD = mD < hc;
+  if (!hasC && !hasD) return kSink;
+  int kC = kSink, kD = kSink;
+  if (hasC) {
+    const unsigned eq = (x[1] == mC ? 1u : 0u) | (x[3] == mC ? 2u : 0u) | (x[4] == mC ? 4u : 0u) |
+                        (x[6] == mC ? 8u : 0u);
+    const bool next = x[1] == mC + 1 || x[3] == mC + 1 || x[4] == mC + 1 || x[6] == mC + 1;
+    if ((eq & (eq - 1u)) != 0 || next || (hc >> 20) - (mC >> 20) > 18u) return -1;
+    kC = (int)((0x6431u >> (4 * (__ffs(eq) - 1))) & 15u);
+  }
+  if (hasD) {
+    const unsigned eq = (x[0] == mD ? 1u : 0u) | (x[2] == mD ? 2u : 0u) | (x[5] == mD ? 4u : 0u) |
+                        (x[7] == mD ? 8u : 0u);
+    const bool next = x[0] == mD + 1 || x[2] == mD + 1 || x[5] == mD + 1 || x[7] == mD + 1;
+    if ((eq & (eq - 1u)) != 0 || next || (hc >> 20) - (mD >> 20) > 18u) return -1;
+    kD = (int)((0x7520u >> (4 * (__ffs(eq) - 1))) & 15u);
+  }
+  if (!hasD) return kC;
+  if (!hasC) return kD;
+  // both minima are within 18 binades of h_c, hence in the float range
+  const float fc = __uint_as_float((hc - (896u << 20)) << 3);
+  const float fC = __uint_as_float((mC - (896u << 20)) << 3);
+  const float fD = __uint_as_float((mD - (896u << 20)) << 3);
+  const float sC = __fsub_rn(fc, fC);
+  const float sD = __fmul_rn(__fsub_rn(fc, fD), 0.70710677f);
+  const float tol = __fmul_rn(__fadd_rn(fc, fmaxf(sC, sD)), 1.52587890625e-05f);  // 2^-16
+  if (__fsub_rn(sC, sD) > tol) return kC;
+  if (__fsub_rn(sD, sC) > tol) return kD;
+  return -1;
+}
+
 template <typename HT>
 __device__ __forceinline__ int receiver_code_vals(const HT hcv, const HT* v) {
   using B = Bits<HT>;
   using U = typename B::U;
+  if constexpr (sizeof(HT) == 8) {
+    const int k = receiver_code_hi(hcv, v);
+    if (k >= 0) return k;
+  }
   const U bc = B::of(hcv);
   U mC = bc, mD = bc, rC = bc, rD = bc;  // group minima and runners-up below hc
   int kC = kSink, kD = kSink;
