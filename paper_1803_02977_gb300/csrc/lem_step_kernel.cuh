@@ -192,41 +192,33 @@ __device__ __forceinline__ int receiver_code_hi(const double hcd, const double* 
   unsigned worst = hc;
 #pragma unroll
   for (int k = 0; k < 8; ++k) worst = max(worst, x[k]);
-  // non-negative, finite, and h_c (and anything within 18 binades below it)
-  // within the float exponent range
-  if (worst >= 0x7FF00000u || hc < (915u << 20) || hc >= (1151u << 20)) return -1;
   const unsigned mC = min(min(x[1], x[3]), min(x[4], x[6]));
   const unsigned mD = min(min(x[0], x[2]), min(x[5], x[7]));
-  if (mC == hc || mD == hc) return -1;
   const bool hasC = mC < hc, hasD = mD < hc;
-  if (!hasC && !hasD) return kSink;
-  int kC = kSink, kD = kSink;
-  if (hasC) {
-    const unsigned eq = (x[1] == mC ? 1u : 0u) | (x[3] == mC ? 2u : 0u) | (x[4] == mC ? 4u : 0u) |
-                        (x[6] == mC ? 8u : 0u);
-    const bool next = x[1] == mC + 1 || x[3] == mC + 1 || x[4] == mC + 1 || x[6] == mC + 1;
-    if ((eq & (eq - 1u)) != 0 || next || (hc >> 20) - (mC >> 20) > 18u) return -1;
-    kC = (int)((0x6431u >> (4 * (__ffs(eq) - 1))) & 15u);
-  }
-  if (hasD) {
-    const unsigned eq = (x[0] == mD ? 1u : 0u) | (x[2] == mD ? 2u : 0u) | (x[5] == mD ? 4u : 0u) |
-                        (x[7] == mD ? 8u : 0u);
-    const bool next = x[0] == mD + 1 || x[2] == mD + 1 || x[5] == mD + 1 || x[7] == mD + 1;
-    if ((eq & (eq - 1u)) != 0 || next || (hc >> 20) - (mD >> 20) > 18u) return -1;
-    kD = (int)((0x7520u >> (4 * (__ffs(eq) - 1))) & 15u);
-  }
-  if (!hasD) return kC;
-  if (!hasC) return kD;
-  // both minima are within 18 binades of h_c, hence in the float range
+  const unsigned eqC = (x[1] == mC ? 1u : 0u) | (x[3] == mC ? 2u : 0u) | (x[4] == mC ? 4u : 0u) |
+                       (x[6] == mC ? 8u : 0u);
+  const unsigned eqD = (x[0] == mD ? 1u : 0u) | (x[2] == mD ? 2u : 0u) | (x[5] == mD ? 4u : 0u) |
+                       (x[7] == mD ? 8u : 0u);
+  const bool nextC = x[1] == mC + 1 || x[3] == mC + 1 || x[4] == mC + 1 || x[6] == mC + 1;
+  const bool nextD = x[0] == mD + 1 || x[2] == mD + 1 || x[5] == mD + 1 || x[7] == mD + 1;
+  const bool badC = (eqC & (eqC - 1u)) != 0 || nextC || (hc >> 20) - (mC >> 20) > 18u;
+  const bool badD = (eqD & (eqD - 1u)) != 0 || nextD || (hc >> 20) - (mD >> 20) > 18u;
+  const int kC = (int)((0x6431u >> (4 * (__ffs(eqC) - 1))) & 15u);
+  const int kD = (int)((0x7520u >> (4 * (__ffs(eqD) - 1))) & 15u);
+  // slopes in FP32 from the high words (meaningful only when both minima
+  // are within 18 binades of h_c, which the checks below require)
   const float fc = __uint_as_float((hc - (896u << 20)) << 3);
-  const float fC = __uint_as_float((mC - (896u << 20)) << 3);
-  const float fD = __uint_as_float((mD - (896u << 20)) << 3);
-  const float sC = __fsub_rn(fc, fC);
-  const float sD = __fmul_rn(__fsub_rn(fc, fD), 0.70710677f);
+  const float sC = __fsub_rn(fc, __uint_as_float((mC - (896u << 20)) << 3));
+  const float sD = __fmul_rn(__fsub_rn(fc, __uint_as_float((mD - (896u << 20)) << 3)), 0.70710677f);
   const float tol = __fmul_rn(__fadd_rn(fc, fmaxf(sC, sD)), 1.52587890625e-05f);  // 2^-16
-  if (__fsub_rn(sC, sD) > tol) return kC;
-  if (__fsub_rn(sD, sC) > tol) return kD;
-  return -1;
+  const bool cWins = __fsub_rn(sC, sD) > tol, dWins = __fsub_rn(sD, sC) > tol;
+  // non-negative, finite, h_c (and anything within 18 binades below it) in
+  // the float exponent range, and no neighbour group sharing h_c's high word
+  const bool undecided = worst >= 0x7FF00000u || hc < (915u << 20) || hc >= (1151u << 20) ||
+                         mC == hc || mD == hc || (hasC && badC) || (hasD && badD) ||
+                         (hasC && hasD && !cWins && !dWins);
+  const int code = !hasC ? (hasD ? kD : kSink) : (!hasD ? kC : (cWins ? kC : kD));
+  return undecided ? -1 : code;
 }
 
 template <typename HT>
@@ -301,7 +293,40 @@ __device__ __forceinline__ bool f32_group_safe(const float* v, const int* ks, fl
   return no_rounding_merge<float>(bm, r, bc);
 }
 
+// The common case of receiver_code_f32_vals without branches: returns the
+// code when every condition of its fast path holds (finite non-negative
+// values, group minima nonzero and within 27 binades of h_c, FP32 slopes
+// apart by more than 2^-18), else -1.
+__device__ __forceinline__ int receiver_f32_fast(const float hc, const float* v) {
+  const unsigned bc = __float_as_uint(hc);
+  unsigned worst = bc;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) worst = max(worst, __float_as_uint(v[k]));
+  const float mC = fminf(fminf(v[1], v[3]), fminf(v[4], v[6]));
+  const float mD = fminf(fminf(v[0], v[2]), fminf(v[5], v[7]));
+  const bool hasC = mC < hc, hasD = mD < hc;
+  const int kC = v[1] == mC ? 1 : (v[3] == mC ? 3 : (v[4] == mC ? 4 : 6));
+  const int kD = v[0] == mD ? 0 : (v[2] == mD ? 2 : (v[5] == mD ? 5 : 7));
+  const unsigned bmC = __float_as_uint(mC), bmD = __float_as_uint(mD);
+  const int ec = (int)(bc >> 23);
+  const bool okC = bmC != 0 && ec - max((int)(bmC >> 23), 1) <= 27;
+  const bool okD = bmD != 0 && ec - max((int)(bmD >> 23), 1) <= 27;
+  const float sC = __fsub_rn(hc, mC);
+  const float sD = __fmul_rn(__fsub_rn(hc, mD), 0.70710677f);
+  const bool cWins = sC > __fmul_rn(sD, 1.000003814697265625f);
+  const bool dWins = sD > __fmul_rn(sC, 1.000003814697265625f);
+  const bool both = hasC && hasD;
+  const bool undecided = worst >= Bits<float>::kInf || (hasC && !okC) || (hasD && !okD) ||
+                         (both && (!(fminf(sC, sD) > 1e-30f) || (!cWins && !dWins)));
+  const int code = !hasC ? (hasD ? kD : kSink) : (!hasD ? kC : (cWins ? kC : kD));
+  return undecided ? -1 : code;
+}
+
 __device__ __forceinline__ int receiver_code_f32_vals(const float hc, const float* v) {
+  {
+    const int k = receiver_f32_fast(hc, v);
+    if (k >= 0) return k;
+  }
   unsigned worst = Bits<float>::of(hc);
 #pragma unroll
   for (int k = 0; k < 8; ++k) worst = max(worst, Bits<float>::of(v[k]));
