@@ -86,6 +86,29 @@ __device__ __forceinline__ void push_tile_roots_device(const uint8_t* code, int*
   }
 }
 
+// Erosion parameters of the warp tier, copied out of the kernel parameter
+// once per tile so that stores to h do not force them to be reloaded.  All
+// of a warp forest's counts are below kTableN: g always comes from a table.
+template <typename HT>
+struct TileErode {
+  const void* gtab;  // F/(1+F): double2 {F, g} (FP64) or float (FP32)
+  const double* Uf;
+  double Udt, dt;
+  float Udt_f;
+  __device__ __forceinline__ HT operator()(int c, int k, unsigned count, HT hcur, HT hr) const {
+    const int i = (nbr_diag(k) ? kTableN : 0) + (int)count;
+    if constexpr (sizeof(HT) == 8) {
+      const double g = static_cast<const double2*>(gtab)[i].y;
+      const double h0 = __dadd_rn(hcur, Uf ? __dmul_rn(Uf[c], dt) : Udt);
+      return __fma_rn(-g, __dsub_rn(h0, hr), h0);
+    } else {
+      const float g = static_cast<const float*>(gtab)[i];
+      const float h0 = __fadd_rn(hcur, Uf ? (float)__dmul_rn(Uf[c], dt) : Udt_f);
+      return __fmaf_rn(-g, __fsub_rn(h0, hr), h0);
+    }
+  }
+};
+
 // Algs 3-6 on the trees rooted in `tile`, by one warp.  off[k] is the
 // address offset of neighbour k.  Returns the number of cells handled, or -1
 // if the forest does not fit (nothing was written).
@@ -177,7 +200,12 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
       const int pc = __shfl_sync(0xffffffffu, c, s);
       const int pex = __shfl_sync(0xffffffffu, incl - k, s);
       if (e < tot) {
-        for (int r = e - pex; r > 0; --r) pm &= pm - 1;
+        // drop the r = e - pex lowest set bits (pm has more than r set bits)
+        const int r = e - pex;
+        if (r > 0) pm &= pm - 1;
+        if (r > 1) pm &= pm - 1;
+        if (r > 2) pm &= pm - 1;
+        for (int t = 3; t < r; ++t) pm &= pm - 1;
         const int kk = __ffs(pm) - 1;
         const int pos = tail + e;
         const int cc = pc + off[kk];
@@ -219,14 +247,24 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
   }
   __syncwarp();
   // Alg 6 from level 1 up: the receiver's new elevation is the parent's v
+  TileErode<HT> ero;
+  if constexpr (sizeof(HT) == 8) {
+    ero.gtab = a.Ftab;
+  } else {
+    ero.gtab = a.gtab;
+  }
+  ero.Uf = a.Uf;
+  ero.Udt = a.Udt;
+  ero.dt = a.dt;
+  ero.Udt_f = a.Udt_f;
+  HT* const hh = a.h;
   for (int l = 1; l < L; ++l) {
     const int l0 = q.lev[l], l1 = q.lev[l + 1];
     for (int jj = l0 + lane; jj < l1; jj += 32) {
       const int c = q.c[jj];
       const unsigned pd = q.pd[jj];
-      const HT hn = erode_value(a, c, (int)(pd & 15u), (CT)(pd >> 16), q.v[jj],
-                                q.v[(pd >> 4) & 0xFFFu]);
-      a.h[c] = hn;
+      const HT hn = ero(c, (int)(pd & 15u), pd >> 16, q.v[jj], q.v[(pd >> 4) & 0xFFFu]);
+      hh[c] = hn;
       q.v[jj] = hn;
     }
     __syncwarp();
