@@ -764,14 +764,21 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
   HT* S = reinterpret_cast<HT*>(dyn_smem + w * kWarpBytes);
   unsigned long long* bar =
       reinterpret_cast<unsigned long long*>(dyn_smem + (w + 1) * kWarpBytes - 16);
+  // fields of the kernel parameter used in the loop, held in registers
+  // (the code and mask stores would otherwise force reloads)
   const int nx = a.nx, ny = a.ny;
+  const bool frozen = a.frozen != 0;
+  const HT* const h = a.h;
+  uint8_t* const code = a.code;
+  uint8_t* const mask = a.mask;
+  DevState* const st = a.st;
   const int nsx = (nx + kStripOut - 1) / kStripOut;
   const int units = nsx * ((ny + kStripRows - 1) / kStripRows);
   // TMA staging: one box load per strip, issued by lane 0, completing on the
   // warp's mbarrier (phase parity alternates per strip)
   // (the box destination must be 128-byte aligned; a warp whose slice is
   // not stages element-wise instead)
-  const bool tma = a.has_tmap && !a.frozen && (smem_u32(S) & 127u) == 0;
+  const bool tma = a.has_tmap && !frozen && (smem_u32(S) & 127u) == 0;
   if (tma && lane == 0) mbar_init(bar, 1);
   __syncwarp();
   unsigned parity = 0;
@@ -793,14 +800,14 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
         mbar_expect_tx(bar, (unsigned)(kStageRows * kStageCols * sizeof(HT)));
         tma_load_2d(S, &a.tmap, xb, yb, bar);
       }
-      ok = __all_sync(0xffffffffu, mbar_wait(bar, parity, a.st));
+      ok = __all_sync(0xffffffffu, mbar_wait(bar, parity, st));
       parity ^= 1u;
       if (!ok) break;
-    } else if (!a.frozen) {
-      stage_strip(a.h, nx, ny, xb, yb, S, lane);
+    } else if (!frozen) {
+      stage_strip(h, nx, ny, xb, yb, S, lane);
     }
     HT ul = HT(0), uc = HT(0), ur = HT(0), ml = HT(0), mc = HT(0), mr = HT(0);
-    if (!a.frozen) {
+    if (!frozen) {
       ul = S[sc - 1];
       uc = S[sc];
       ur = S[sc + 1];
@@ -812,7 +819,7 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
     for (int y = y0 - 1; y <= y1; ++y) {
       int cd = 0xFF;
       const bool yin = y >= 0 && y < ny;
-      if (!a.frozen) {
+      if (!frozen) {
         const HT* Sd = S + (y + 1 - yb) * kStageCols + sc;
         const HT dl = Sd[-1], dc = Sd[0], dr = Sd[1];
         if (xin && yin) {
@@ -822,18 +829,18 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
             const HT v[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
             cd = receiver_from(mc, v);
           }
-          if (own && y >= y0 && y < y1) a.code[(size_t)y * nx + x] = (uint8_t)cd;
+          if (own && y >= y0 && y < y1) code[(size_t)y * nx + x] = (uint8_t)cd;
         }
         ul = ml; uc = mc; ur = mr;
         ml = dl; mc = dc; mr = dr;
       } else if (xin && yin) {
-        cd = a.code[(size_t)y * nx + x];
+        cd = code[(size_t)y * nx + x];
       }
       cw = ((cw >> 8) & 0xFFFFu) | ((unsigned)cd << 16);
       const unsigned cl = __shfl_up_sync(0xffffffffu, cw, 1);
       const unsigned cr = __shfl_down_sync(0xffffffffu, cw, 1);
       if (own && y - 1 >= y0 && y - 1 < y1)
-        a.mask[(size_t)(y - 1) * nx + x] = (uint8_t)mask_from_packed(cl, cw, cr);
+        mask[(size_t)(y - 1) * nx + x] = (uint8_t)mask_from_packed(cl, cw, cr);
     }
     __syncwarp();  // S is restaged by the next unit
   }

@@ -95,6 +95,14 @@ struct TileErode {
   const double* Uf;
   double Udt, dt;
   float Udt_f;
+  // Alg 5: h + dt*U (the same operations as uplift_sink)
+  __device__ __forceinline__ HT uplift(int c, HT hcur) const {
+    if constexpr (sizeof(HT) == 8) {
+      return __dadd_rn(hcur, Uf ? __dmul_rn(Uf[c], dt) : Udt);
+    } else {
+      return __fadd_rn(hcur, Uf ? (float)__dmul_rn(Uf[c], dt) : Udt_f);
+    }
+  }
   __device__ __forceinline__ HT operator()(int c, int k, unsigned count, HT hcur, HT hr) const {
     const int i = (nbr_diag(k) ? kTableN : 0) + (int)count;
     if constexpr (sizeof(HT) == 8) {
@@ -116,19 +124,23 @@ template <typename HT, typename CT>
 __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const TileQ<HT>& q,
                                            const int* off, int tile, int lane) {
   using Q = TileQ<HT>;
-  const int nx = a.nx, ny = a.ny;
+  // fields of the kernel parameter used in the loops, held in registers
+  // (stores through other pointers would otherwise force reloads)
+  const int nx = a.nx, ny = a.ny, tiles_x = a.tiles_x;
   const unsigned lt = (1u << lane) - 1u;
-  const uint8_t* mask = a.mask;
+  const uint8_t* const mask = a.mask;
+  const uint8_t* const code = a.code;
+  const HT* const h = a.h;
   // level 0: the tile's cells without receiver, in row order
   int n = 0;
   {
-    const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
     const int x = tx * kTileW + lane, y0 = ty * kTileH;
     int cd[kTileH];
 #pragma unroll
     for (int r = 0; r < kTileH; ++r) {
       const int y = y0 + r;
-      cd[r] = (x < nx && y < ny) ? a.code[(size_t)y * nx + x] : 0;
+      cd[r] = (x < nx && y < ny) ? code[(size_t)y * nx + x] : 0;
     }
 #pragma unroll
     for (int r = 0; r < kTileH; ++r) {
@@ -139,7 +151,7 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
         const int c = (y0 + r) * nx + x;
         q.c[pos] = c;
         q.pd[pos] = (unsigned)cd[r];
-        cp_async_elem(q.v + pos, a.h + c, true);
+        cp_async_elem(q.v + pos, h + c, true);
       }
       n += __popc(bal);
     }
@@ -211,7 +223,7 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
         const int cc = pc + off[kk];
         q.c[pos] = cc;
         q.pd[pos] = (1u << 16) | ((unsigned)(head + s) << 4) | (unsigned)(7 - kk);
-        cp_async_elem(q.v + pos, a.h + cc, true);
+        cp_async_elem(q.v + pos, h + cc, true);
       }
     }
     tail += tot;
@@ -231,22 +243,6 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
   }
   cp_async_wait_all();  // every entry's elevation has arrived
   __syncwarp();
-  // Alg 5 on level 0: pits are uplifted, the perimeter stays
-  for (int jj = lane; jj < n; jj += 32) {
-    HT hc = q.v[jj];
-    if ((q.pd[jj] & 15u) == (unsigned)kSink) {
-      const int c = q.c[jj];
-      if constexpr (sizeof(HT) == 8) {
-        hc = __dadd_rn(hc, uplift_dt(a, c));
-      } else {
-        hc = __fadd_rn(hc, uplift_dt_f(a, c));
-      }
-      a.h[c] = hc;
-      q.v[jj] = hc;
-    }
-  }
-  __syncwarp();
-  // Alg 6 from level 1 up: the receiver's new elevation is the parent's v
   TileErode<HT> ero;
   if constexpr (sizeof(HT) == 8) {
     ero.gtab = a.Ftab;
@@ -258,6 +254,17 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
   ero.dt = a.dt;
   ero.Udt_f = a.Udt_f;
   HT* const hh = a.h;
+  // Alg 5 on level 0: pits are uplifted, the perimeter stays
+  for (int jj = lane; jj < n; jj += 32) {
+    if ((q.pd[jj] & 15u) == (unsigned)kSink) {
+      const int c = q.c[jj];
+      const HT hc = ero.uplift(c, q.v[jj]);
+      hh[c] = hc;
+      q.v[jj] = hc;
+    }
+  }
+  __syncwarp();
+  // Alg 6 from level 1 up: the receiver's new elevation is the parent's v
   for (int l = 1; l < L; ++l) {
     const int l0 = q.lev[l], l1 = q.lev[l + 1];
     for (int jj = l0 + lane; jj < l1; jj += 32) {
