@@ -174,7 +174,7 @@ StepArgs<HT, CT> make_args(lem_ctx* c, int phases, int nsteps) {
   a.cntq = (CT*)c->cntq;
   a.pcap = c->pcap;
   a.tiles_x = (c->p.nx + kTileW - 1) / kTileW;
-  a.ntiles = a.tiles_x * ((c->p.ny + kTileH - 1) / kTileH);
+  a.ntiles = a.tiles_x * ((c->p.ny + tile_h<HT>() - 1) / tile_h<HT>());
   a.has_tmap = c->tmap_ok ? 1 : 0;
   a.tmap = c->tmap;
   a.Udt = c->p.U * c->p.dt;

@@ -94,7 +94,12 @@ constexpr int kStage = 16384;      // emitted entries staged in shared memory pe
 constexpr int kMaxPrivLevels = 2048;  // level offsets a private queue may hold
 constexpr int kOvfCap = 256;       // tiles a block keeps for its block tier
 constexpr int kTileW = 32;         // warp-tier tile width: one column per lane
-constexpr int kTileH = 8;          // warp-tier tile height
+// warp-tier tile height: 8 rows with FP64 elevations, 12 with FP32 (whose
+// queue entries are smaller, so a warp holds more of them)
+template <typename HT>
+__host__ __device__ constexpr int tile_h() {
+  return sizeof(HT) == 4 ? 12 : 8;
+}
 constexpr int kWarpBytes = 7040;   // shared memory per warp for its forest
 constexpr int kTileLv = 127;       // levels a warp forest may hold
 constexpr int kTileLvBytes = 256;  // its level offsets, u16 [0, kTileLv]

@@ -2,7 +2,7 @@
 //
 // Included by lem_step_kernel.cuh after the phase functions it builds on.
 //
-// The grid is cut into tiles of kTileW x kTileH cells.  A warp takes one
+// The grid is cut into tiles of kTileW x tile_h<HT>() cells.  A warp takes one
 // tile at a time and handles every tree rooted at one of the tile's cells
 // without receiver (level 0 of Alg 3): it grows their breadth-first levels
 // (Alg 3), pushes cell counts from the deepest level up (Alg 4) and erodes
@@ -35,7 +35,7 @@ struct TileQ {
   static constexpr int kHead = kTileLvBytes;
   static constexpr int kEntryBytes = (int)sizeof(HT) + 4 + 4;
   static constexpr int kCap = ((kWarpBytes - kHead) / kEntryBytes) & ~7;
-  static_assert(kCap >= kTileW * kTileH, "a tile's level 0 always fits");
+  static_assert(kCap >= kTileW * tile_h<HT>(), "a tile's level 0 always fits");
   static_assert(kCap < (1 << 12), "parent index and count fit pd");
   static_assert(kHead % 16 == 0, "entry arrays stay aligned");
   unsigned short* lev;
@@ -56,26 +56,28 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // Level 0 of one tile as seen by lane `lane`: the row codes of its column.
 // Out-of-grid positions read as 0 (a cell with a receiver: never a root).
+template <int TH>
 __device__ __forceinline__ void tile_codes(const uint8_t* code, int tile, int tiles_x, int nx,
                                            int ny, int lane, int* cd, int* x, int* y0) {
   const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
   *x = tx * kTileW + lane;
-  *y0 = ty * kTileH;
+  *y0 = ty * TH;
 #pragma unroll
-  for (int r = 0; r < kTileH; ++r) {
+  for (int r = 0; r < TH; ++r) {
     const int y = *y0 + r;
     cd[r] = (*x < nx && y < ny) ? code[(size_t)y * nx + *x] : 0;
   }
 }
 
 // Append the roots of `tile` to the device tier's level 0 (queue[0, n)).
+template <int TH>
 __device__ __forceinline__ void push_tile_roots_device(const uint8_t* code, int* queue,
                                                        int* dev_roots, int tile, int tiles_x,
                                                        int nx, int ny, int lane) {
-  int cd[kTileH], x, y0;
-  tile_codes(code, tile, tiles_x, nx, ny, lane, cd, &x, &y0);
+  int cd[TH], x, y0;
+  tile_codes<TH>(code, tile, tiles_x, nx, ny, lane, cd, &x, &y0);
 #pragma unroll
-  for (int r = 0; r < kTileH; ++r) {
+  for (int r = 0; r < TH; ++r) {
     const bool f = cd[r] >= kSink;
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     if (bal == 0) continue;
@@ -135,15 +137,16 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
   int n = 0;
   {
     const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-    const int x = tx * kTileW + lane, y0 = ty * kTileH;
-    int cd[kTileH];
+    constexpr int TH = tile_h<HT>();
+    const int x = tx * kTileW + lane, y0 = ty * TH;
+    int cd[TH];
 #pragma unroll
-    for (int r = 0; r < kTileH; ++r) {
+    for (int r = 0; r < TH; ++r) {
       const int y = y0 + r;
       cd[r] = (x < nx && y < ny) ? code[(size_t)y * nx + x] : 0;
     }
 #pragma unroll
-    for (int r = 0; r < kTileH; ++r) {
+    for (int r = 0; r < TH; ++r) {
       const bool f = cd[r] >= kSink;
       const unsigned bal = __ballot_sync(0xffffffffu, f);
       if (f) {
@@ -290,11 +293,12 @@ __device__ __noinline__ int block_tier(const StepArgs<HT, CT>& a, Shared& s, int
   int* pq = a.pq + (size_t)b * a.pcap;
   uint8_t* pqm = a.pqm + (size_t)b * a.pcap;
   uint8_t* pqk = a.pqk + (size_t)b * a.pcap;
+  constexpr int TH = tile_h<HT>();
   for (int i = w; i < nov; i += kWarps) {
-    int cd[kTileH], x, y0;
-    tile_codes(a.code, s.ovf_tiles[i], a.tiles_x, nx, ny, lane, cd, &x, &y0);
+    int cd[TH], x, y0;
+    tile_codes<TH>(a.code, s.ovf_tiles[i], a.tiles_x, nx, ny, lane, cd, &x, &y0);
 #pragma unroll
-    for (int r = 0; r < kTileH; ++r) {
+    for (int r = 0; r < TH; ++r) {
       const bool f = cd[r] >= kSink;
       const unsigned bal = __ballot_sync(0xffffffffu, f);
       if (bal == 0) continue;
@@ -315,7 +319,8 @@ __device__ __noinline__ int block_tier(const StepArgs<HT, CT>& a, Shared& s, int
   const int done = (n0 <= a.pcap) ? private_forest(a, s, n0) : -1;
   if (done >= 0) return done;
   for (int i = w; i < nov; i += kWarps)
-    push_tile_roots_device(a.code, a.queue, dev_roots, s.ovf_tiles[i], a.tiles_x, nx, ny, lane);
+    push_tile_roots_device<TH>(a.code, a.queue, dev_roots, s.ovf_tiles[i], a.tiles_x, nx, ny,
+                               lane);
   return 0;
 }
 
@@ -358,7 +363,8 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
     if (i < kOvfCap) {
       if (lane == 0) s.ovf_tiles[i] = cur;
     } else {
-      push_tile_roots_device(a.code, a.queue, dev_roots, cur, a.tiles_x, a.nx, a.ny, lane);
+      push_tile_roots_device<tile_h<HT>()>(a.code, a.queue, dev_roots, cur, a.tiles_x, a.nx,
+                                           a.ny, lane);
     }
   }
   // per-warp totals (lane 0's count is the warp's)
