@@ -764,7 +764,6 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
                 "strip and barrier fit the warp slice");
   constexpr int kAlign = 16 / (int)sizeof(HT);  // staged start: a 16-byte multiple
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int gw = blockIdx.x * kWarps + w, nw = (int)gridDim.x * kWarps;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   HT* S = reinterpret_cast<HT*>(dyn_smem + w * kWarpBytes);
   unsigned long long* bar =
@@ -779,6 +778,16 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
   DevState* const st = a.st;
   const int nsx = (nx + kStripOut - 1) / kStripOut;
   const int units = nsx * ((ny + kStripRows - 1) / kStripRows);
+  // each block takes an equal contiguous range of strips, its warps claim
+  // them one at a time (the next claim issued before the current strip)
+  __shared__ int s_next;
+  const int G = (int)gridDim.x, b = blockIdx.x;
+  const int u1 = (int)((long long)units * (b + 1) / G);
+  if (threadIdx.x == 0) s_next = (int)((long long)units * b / G);
+  __syncthreads();
+  int u = 0;
+  if (lane == 0) u = atomicAdd(&s_next, 1);
+  u = __shfl_sync(0xffffffffu, u, 0);
   // TMA staging: one box load per strip, issued by lane 0, completing on the
   // warp's mbarrier (phase parity alternates per strip)
   // (the box destination must be 128-byte aligned; a warp whose slice is
@@ -788,7 +797,9 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
   __syncwarp();
   unsigned parity = 0;
   bool ok = true;
-  for (int u = gw; ok && u < units; u += nw) {
+  while (ok && u < u1) {
+    int next = 0;
+    if (lane == 0) next = atomicAdd(&s_next, 1);
     const int sy = u / nsx, sx = u - sy * nsx;
     const int x0 = sx * kStripOut;  // first owned column
     const int x = x0 - 1 + lane;    // this lane's column
@@ -848,6 +859,7 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
         mask[(size_t)(y - 1) * nx + x] = (uint8_t)mask_from_packed(cl, cw, cr);
     }
     __syncwarp();  // S is restaged by the next unit
+    u = __shfl_sync(0xffffffffu, next, 0);
   }
   __syncwarp();
   if (tma && lane == 0 && ok) mbar_inval(bar);
