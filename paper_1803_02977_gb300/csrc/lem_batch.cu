@@ -7,10 +7,14 @@
 // Each thread block repeatedly claims the largest realization not yet taken
 // (realizations are sorted by cell count; a device counter hands them out, so
 // blocks are scheduled longest-first) and runs all of its time steps alone
-// with block barriers: a realization's whole forest is the block's private
-// forest, so no device-wide barrier is ever needed.  Elevations are FP32 with
-// FP64 receiver slope tests (see receiver_code), erosion in the increment
-// form with g = F/(1+F) from a per-realization shared-memory table.
+// with block barriers, so no device-wide barrier is ever needed.  Inside a
+// realization the step takes the same tiered form as lem_step: the block's
+// warps compute receiver codes and donor masks strip by strip (Algs 1-2),
+// then run Algs 3-6 on warp-private tile forests in shared memory; tiles
+// whose forest does not fit are finished on the block-wide forest of the
+// realization (lem_forest.cuh), whose queue holds the whole grid.
+// Elevations are FP32 with FP64 receiver slope tests for near ties, erosion
+// in the increment form with g = F/(1+F) from a per-realization table.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -19,6 +23,7 @@
 
 #include "lem.h"
 #include "lem_forest.cuh"
+#include "lem_tiles.cuh"
 
 using namespace lem;
 
@@ -35,6 +40,7 @@ struct BatchArgs {
   const double* m;
   const double* dx;
   const float* Udt;
+  const float* gtab;       // F/(1+F) by count: realization r at r * 2 * kBatchTN
   const int* order;        // realizations, largest first
   int* next;               // claim counter
   float* h;
@@ -49,12 +55,32 @@ struct BatchArgs {
   int nsteps;
 };
 
+// g = F/(1+F) for counts below kBatchTN, F = K*dt*(count*dx^2)^m / d (the
+// same operation order as the single-grid tables).
+__global__ void batch_tables_kernel(float* gtab, int R, const double* Kdt, const double* m,
+                                    const double* dx) {
+  const long long total = (long long)R * kBatchTN;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / kBatchTN), cnt = (int)(i - (long long)r * kBatchTN);
+    const double ddx = dx[r], ddd = ddx * kSqrt2, area = ddx * ddx;
+    const double P = Kdt[r] * pow((double)cnt * area, m[r]);
+    const double Fc = P / ddx, Fd = P / ddd;
+    gtab[(size_t)r * 2 * kBatchTN + cnt] = (float)(Fc / (1.0 + Fc));
+    gtab[(size_t)r * 2 * kBatchTN + kBatchTN + cnt] = (float)(Fd / (1.0 + Fd));
+  }
+}
+
 template <int BD, int PI>
 __global__ void __launch_bounds__(BD) lem_batch_kernel(BatchArgs a) {
+  constexpr int TH = tile_h<float>();
   __shared__ ForestSmem<BD, PI> s;
-  __shared__ float tab[2 * kBatchTN];
-  __shared__ int s_r;
-  const int t = threadIdx.x;
+  __shared__ int s_r, s_next, s_n_ovf, s_n0;
+  __shared__ int s_off[8];
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  float* S = reinterpret_cast<float*>(dyn_smem + w * kWarpBytes);
+  const TileQ<float> q(dyn_smem + w * kWarpBytes);
   while (true) {
     if (t == 0) {
       const int i = atomicAdd(a.next, 1);
@@ -79,6 +105,7 @@ __global__ void __launch_bounds__(BD) lem_batch_kernel(BatchArgs a) {
     g.cntq = a.cntq + o;
     g.plev = a.plev + o + r;
     g.Udt = a.Udt[r];
+    const float* tab = a.gtab + (size_t)r * 2 * kBatchTN;
     ErosionFactors ef;
     ef.tab = tab;
     ef.TN = kBatchTN;
@@ -87,18 +114,85 @@ __global__ void __launch_bounds__(BD) lem_batch_kernel(BatchArgs a) {
     ef.dx = a.dx[r];
     ef.dxd = ef.dx * kSqrt2;
     ef.area = ef.dx * ef.dx;
-    for (int i = t; i < kBatchTN; i += BD) {
-      const double P = ef.Kdt * pow((double)i * ef.area, ef.m);
-      const double Fc = P / ef.dx, Fd = P / ef.dxd;
-      tab[i] = (float)(Fc / (1.0 + Fc));
-      tab[kBatchTN + i] = (float)(Fd / (1.0 + Fd));
-    }
-    __syncthreads();
+    TileArgs<float> ta;
+    ta.nx = g.nx;
+    ta.ny = g.ny;
+    ta.tiles_x = (g.nx + kTileW - 1) / kTileW;
+    ta.code = g.code;
+    ta.mask = g.mask;
+    ta.h = g.h;
+    ta.ero.gtab = tab;
+    ta.ero.tn = kBatchTN;
+    ta.ero.Uf = nullptr;
+    ta.ero.Udt = (double)g.Udt;
+    ta.ero.dt = 0.0;
+    ta.ero.Udt_f = g.Udt;
+    const int ntiles = ta.tiles_x * ((g.ny + TH - 1) / TH);
+    const int nsx = (g.nx + kStripOut - 1) / kStripOut;
+    const int units = nsx * ((g.ny + kStripRows - 1) / kStripRows);
+    if (t < 8) s_off[t] = nbr_off(t, g.nx);
     for (int step = 0; step < a.nsteps; ++step) {
-      const int n0 = forest_receivers<BD, PI>(g, s);
-      const int PL = forest_levels<BD, PI>(g, n0, s);
-      forest_accumulate<BD>(g, PL);
-      forest_erode<BD>(g, PL, ef);
+      // Algs 1-2: the realization's strips, claimed by the block's warps
+      if (t == 0) s_next = 0;
+      __syncthreads();
+      while (true) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(&s_next, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= units) break;
+        const int sy = u / nsx, sx = u - sy * nsx;
+        const int x0 = sx * kStripOut, y0 = sy * kStripRows;
+        const int xb = (x0 - 2) & ~3;
+        stage_strip(g.h, g.nx, g.ny, xb, y0 - 2, S, lane);
+        codes_strip(S, g.code, g.mask, g.nx, g.ny, x0, y0, xb, false, lane);
+        __syncwarp();
+      }
+      __syncthreads();
+      // Algs 3-6 on warp-private tile forests; tiles that do not fit are
+      // listed in pqf (free until the block-wide forest runs)
+      if (t == 0) {
+        s_next = 0;
+        s_n_ovf = 0;
+        s_n0 = 0;
+      }
+      __syncthreads();
+      while (true) {
+        int tile = 0;
+        if (lane == 0) tile = atomicAdd(&s_next, 1);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= ntiles) break;
+        if (tile_forest(ta, q, s_off, tile, lane) < 0 && lane == 0)
+          g.pqf[atomicAdd(&s_n_ovf, 1)] = tile;
+      }
+      __syncthreads();
+      const int nov = s_n_ovf;
+      if (nov > 0) {
+        // their roots as level 0 of the block-wide forest
+        for (int i = w; i < nov; i += BD / 32) {
+          int cd[TH], x, y0;
+          tile_codes<TH>(g.code, g.pqf[i], ta.tiles_x, g.nx, g.ny, lane, cd, &x, &y0);
+#pragma unroll
+          for (int rr = 0; rr < TH; ++rr) {
+            const bool f = cd[rr] >= kSink;
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (bal == 0) continue;
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&s_n0, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (f) {
+              const int pos = base + __popc(bal & ((1u << lane) - 1u));
+              const int c = (y0 + rr) * g.nx + x;
+              g.pq[pos] = c;
+              g.pqm[pos] = g.mask[c];
+              g.pqk[pos] = (uint8_t)cd[rr];
+            }
+          }
+        }
+        __syncthreads();
+        const int PL = forest_levels<BD, PI>(g, s_n0, s);
+        forest_accumulate<BD>(g, PL);
+        forest_erode<BD>(g, PL, ef);
+      }
       __syncthreads();
     }
   }
@@ -117,9 +211,12 @@ Config config() {
 const Config kConfigs[] = {config<256, 4>(), config<256, 8>(), config<512, 4>(),
                            config<512, 8>(), config<1024, 4>(), config<1024, 8>()};
 
+// dynamic shared memory of a block: one warp slice per warp
+constexpr int dyn_smem_of(int bd) { return (bd / 32) * kWarpBytes; }
+
 template <int BD, int PI>
 cudaError_t launch(int grid, cudaStream_t s, BatchArgs& a) {
-  lem_batch_kernel<BD, PI><<<grid, BD, 0, s>>>(a);
+  lem_batch_kernel<BD, PI><<<grid, BD, dyn_smem_of(BD), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -142,6 +239,7 @@ struct lem_batch {
   long long* d_off = nullptr;
   double *d_Kdt = nullptr, *d_m = nullptr, *d_dx = nullptr;
   float* d_Udt = nullptr;
+  float* gtab = nullptr;  // erosion factors per realization (batch_tables_kernel)
   float* h = nullptr;
   uint8_t *code = nullptr, *mask = nullptr, *pqm = nullptr, *pqk = nullptr;
   int *pq = nullptr, *pqf = nullptr, *cntq = nullptr, *plev = nullptr;
@@ -160,6 +258,7 @@ LEM_API void lem_batch_destroy(lem_batch* b) {
   cudaFree(b->d_m);
   cudaFree(b->d_dx);
   cudaFree(b->d_Udt);
+  cudaFree(b->gtab);
   cudaFree(b->code);
   cudaFree(b->mask);
   cudaFree(b->pq);
@@ -237,6 +336,12 @@ LEM_API int lem_batch_create(lem_batch** out, int R, const int* nx, const int* n
     e = cudaMemcpy(b->d_dx, ddx.data(), R * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_Udt, Udt.data(), R * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->gtab, (size_t)R * 2 * kBatchTN * sizeof(float));
+  if (e == cudaSuccess) {
+    batch_tables_kernel<<<256, 256>>>(b->gtab, R, b->d_Kdt, b->d_m, b->d_dx);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     const int rc = status_of(e);
     lem_batch_destroy(b);
@@ -281,7 +386,10 @@ LEM_API int lem_batch_step(lem_batch* b, int nsteps) {
   if (nsteps == 0) return LEM_OK;
   const Config& c = kConfigs[b->cfg];
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c.fn, c.bd, 0);
+  cudaError_t e = cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       dyn_smem_of(c.bd));
+  if (e != cudaSuccess) return status_of(e);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c.fn, c.bd, dyn_smem_of(c.bd));
   if (e != cudaSuccess) return status_of(e);
   if (per_sm < 1) return LEM_ECUDA;
   int grid = b->nsm * per_sm;
@@ -297,6 +405,7 @@ LEM_API int lem_batch_step(lem_batch* b, int nsteps) {
   a.m = b->d_m;
   a.dx = b->d_dx;
   a.Udt = b->d_Udt;
+  a.gtab = b->gtab;
   a.order = b->d_order;
   a.next = b->d_next;
   a.h = b->h;

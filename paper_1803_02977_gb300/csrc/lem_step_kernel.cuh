@@ -758,6 +758,60 @@ __device__ __forceinline__ int mask_from_packed(unsigned cl, unsigned cw, unsign
                (((eR >> 16) & 1u) << 7));
 }
 
+// Algs 1-2 on one staged strip: S holds rows y0-2 .. y0+kStripRows+1 and
+// columns xb .. xb+kStageCols-1 of the elevations (zero outside the grid).
+// Lane l walks column x0 - 1 + l down the strip with a 3 x 3 window in
+// registers and writes the codes and masks of the owned cells (lanes 1 ..
+// kStripOut, rows y0 .. y0+kStripRows-1, inside the grid).  With frozen
+// receivers the codes are read instead of computed.
+template <typename HT>
+__device__ __forceinline__ void codes_strip(const HT* S, uint8_t* code, uint8_t* mask, int nx,
+                                            int ny, int x0, int y0, int xb, bool frozen,
+                                            int lane) {
+  const int x = x0 - 1 + lane;  // this lane's column
+  const int y1 = min(ny, y0 + kStripRows), yb = y0 - 2;
+  const bool xin = x >= 0 && x < nx;
+  const bool xperim = x == 0 || x == nx - 1;
+  const bool own = lane >= 1 && lane <= kStripOut && xin;
+  const int sc = x - xb;  // staged column of this lane's cell, 1..35
+    HT ul = HT(0), uc = HT(0), ur = HT(0), ml = HT(0), mc = HT(0), mr = HT(0);
+    if (!frozen) {
+      ul = S[sc - 1];
+      uc = S[sc];
+      ur = S[sc + 1];
+      ml = S[kStageCols + sc - 1];
+      mc = S[kStageCols + sc];
+      mr = S[kStageCols + sc + 1];
+    }
+    unsigned cw = 0xFFFFFFFFu;  // codes of rows y-2, y-1, y in bytes 0, 1, 2
+    for (int y = y0 - 1; y <= y1; ++y) {
+      int cd = 0xFF;
+      const bool yin = y >= 0 && y < ny;
+      if (!frozen) {
+        const HT* Sd = S + (y + 1 - yb) * kStageCols + sc;
+        const HT dl = Sd[-1], dc = Sd[0], dr = Sd[1];
+        if (xin && yin) {
+          if (xperim || y == 0 || y == ny - 1) {
+            cd = kEdge;
+          } else {
+            const HT v[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
+            cd = receiver_from(mc, v);
+          }
+          if (own && y >= y0 && y < y1) code[(size_t)y * nx + x] = (uint8_t)cd;
+        }
+        ul = ml; uc = mc; ur = mr;
+        ml = dl; mc = dc; mr = dr;
+      } else if (xin && yin) {
+        cd = code[(size_t)y * nx + x];
+      }
+      cw = ((cw >> 8) & 0xFFFFu) | ((unsigned)cd << 16);
+      const unsigned cl = __shfl_up_sync(0xffffffffu, cw, 1);
+      const unsigned cr = __shfl_down_sync(0xffffffffu, cw, 1);
+      if (own && y - 1 >= y0 && y - 1 < y1)
+        mask[(size_t)(y - 1) * nx + x] = (uint8_t)mask_from_packed(cl, cw, cr);
+    }
+}
+
 template <typename HT, typename CT>
 __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
   static_assert(kStageRows * kStageCols * sizeof(HT) + 16 <= kWarpBytes,
@@ -802,14 +856,9 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
     if (lane == 0) next = atomicAdd(&s_next, 1);
     const int sy = u / nsx, sx = u - sy * nsx;
     const int x0 = sx * kStripOut;  // first owned column
-    const int x = x0 - 1 + lane;    // this lane's column
-    const int y0 = sy * kStripRows, y1 = min(ny, y0 + kStripRows);
-    const bool xin = x >= 0 && x < nx;
-    const bool xperim = x == 0 || x == nx - 1;
-    const bool own = lane >= 1 && lane <= kStripOut && xin;
-    // staged column of this lane's cell: xb is x0 - 2 rounded down
+    const int y0 = sy * kStripRows;
+    // staged columns start at x0 - 2 rounded down to 16 bytes
     const int xb = (x0 - 2) & ~(kAlign - 1), yb = y0 - 2;
-    const int sc = x - xb;  // 1..34
     if (tma) {
       if (lane == 0) {
         fence_proxy_async_smem();  // the previous strip's reads of S come first
@@ -822,42 +871,7 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
     } else if (!frozen) {
       stage_strip(h, nx, ny, xb, yb, S, lane);
     }
-    HT ul = HT(0), uc = HT(0), ur = HT(0), ml = HT(0), mc = HT(0), mr = HT(0);
-    if (!frozen) {
-      ul = S[sc - 1];
-      uc = S[sc];
-      ur = S[sc + 1];
-      ml = S[kStageCols + sc - 1];
-      mc = S[kStageCols + sc];
-      mr = S[kStageCols + sc + 1];
-    }
-    unsigned cw = 0xFFFFFFFFu;  // codes of rows y-2, y-1, y in bytes 0, 1, 2
-    for (int y = y0 - 1; y <= y1; ++y) {
-      int cd = 0xFF;
-      const bool yin = y >= 0 && y < ny;
-      if (!frozen) {
-        const HT* Sd = S + (y + 1 - yb) * kStageCols + sc;
-        const HT dl = Sd[-1], dc = Sd[0], dr = Sd[1];
-        if (xin && yin) {
-          if (xperim || y == 0 || y == ny - 1) {
-            cd = kEdge;
-          } else {
-            const HT v[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
-            cd = receiver_from(mc, v);
-          }
-          if (own && y >= y0 && y < y1) code[(size_t)y * nx + x] = (uint8_t)cd;
-        }
-        ul = ml; uc = mc; ur = mr;
-        ml = dl; mc = dc; mr = dr;
-      } else if (xin && yin) {
-        cd = code[(size_t)y * nx + x];
-      }
-      cw = ((cw >> 8) & 0xFFFFu) | ((unsigned)cd << 16);
-      const unsigned cl = __shfl_up_sync(0xffffffffu, cw, 1);
-      const unsigned cr = __shfl_down_sync(0xffffffffu, cw, 1);
-      if (own && y - 1 >= y0 && y - 1 < y1)
-        mask[(size_t)(y - 1) * nx + x] = (uint8_t)mask_from_packed(cl, cw, cr);
-    }
+    codes_strip(S, code, mask, nx, ny, x0, y0, xb, frozen, lane);
     __syncwarp();  // S is restaged by the next unit
     u = __shfl_sync(0xffffffffu, next, 0);
   }

@@ -93,7 +93,8 @@ __device__ __forceinline__ void push_tile_roots_device(const uint8_t* code, int*
 // of a warp forest's counts are below kTableN: g always comes from a table.
 template <typename HT>
 struct TileErode {
-  const void* gtab;  // F/(1+F): double2 {F, g} (FP64) or float (FP32)
+  const void* gtab;  // F/(1+F): double2 {F, g} (FP64) or float (FP32); diagonal at +tn
+  int tn;            // counts tabulated (every warp-forest count is below it)
   const double* Uf;
   double Udt, dt;
   float Udt_f;
@@ -106,7 +107,7 @@ struct TileErode {
     }
   }
   __device__ __forceinline__ HT operator()(int c, int k, unsigned count, HT hcur, HT hr) const {
-    const int i = (nbr_diag(k) ? kTableN : 0) + (int)count;
+    const int i = (nbr_diag(k) ? tn : 0) + (int)count;
     if constexpr (sizeof(HT) == 8) {
       const double g = static_cast<const double2*>(gtab)[i].y;
       const double h0 = __dadd_rn(hcur, Uf ? __dmul_rn(Uf[c], dt) : Udt);
@@ -119,15 +120,26 @@ struct TileErode {
   }
 };
 
+// What a warp forest reads: the grid, its codes and masks (Algs 1-2 done),
+// the elevations it erodes and the erosion parameters.
+template <typename HT>
+struct TileArgs {
+  int nx, ny, tiles_x;
+  const uint8_t* code;
+  const uint8_t* mask;
+  HT* h;
+  TileErode<HT> ero;
+};
+
 // Algs 3-6 on the trees rooted in `tile`, by one warp.  off[k] is the
 // address offset of neighbour k.  Returns the number of cells handled, or -1
 // if the forest does not fit (nothing was written).
-template <typename HT, typename CT>
-__device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const TileQ<HT>& q,
+template <typename HT>
+__device__ __forceinline__ int tile_forest(const TileArgs<HT>& a, const TileQ<HT>& q,
                                            const int* off, int tile, int lane) {
   using Q = TileQ<HT>;
-  // fields of the kernel parameter used in the loops, held in registers
-  // (stores through other pointers would otherwise force reloads)
+  // the arguments used in the loops, held in registers (stores through other
+  // pointers would otherwise force reloads)
   const int nx = a.nx, ny = a.ny, tiles_x = a.tiles_x;
   const unsigned lt = (1u << lane) - 1u;
   const uint8_t* const mask = a.mask;
@@ -246,16 +258,7 @@ __device__ __forceinline__ int tile_forest(const StepArgs<HT, CT>& a, const Tile
   }
   cp_async_wait_all();  // every entry's elevation has arrived
   __syncwarp();
-  TileErode<HT> ero;
-  if constexpr (sizeof(HT) == 8) {
-    ero.gtab = a.Ftab;
-  } else {
-    ero.gtab = a.gtab;
-  }
-  ero.Uf = a.Uf;
-  ero.Udt = a.Udt;
-  ero.dt = a.dt;
-  ero.Udt_f = a.Udt_f;
+  const TileErode<HT> ero = a.ero;
   HT* const hh = a.h;
   // Alg 5 on level 0: pits are uplifted, the perimeter stays
   for (int jj = lane; jj < n; jj += 32) {
@@ -341,6 +344,23 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
   }
   if (t < 8) s.off[t] = nbr_off(t, a.nx);
   __syncthreads();
+  TileArgs<HT> ta;
+  ta.nx = a.nx;
+  ta.ny = a.ny;
+  ta.tiles_x = a.tiles_x;
+  ta.code = a.code;
+  ta.mask = a.mask;
+  ta.h = a.h;
+  if constexpr (sizeof(HT) == 8) {
+    ta.ero.gtab = a.Ftab;
+  } else {
+    ta.ero.gtab = a.gtab;
+  }
+  ta.ero.tn = kTableN;
+  ta.ero.Uf = a.Uf;
+  ta.ero.Udt = a.Udt;
+  ta.ero.dt = a.dt;
+  ta.ero.Udt_f = a.Udt_f;
   long long mine = 0;
   // tiles are claimed one at a time from a device-wide counter; the next
   // claim is issued before the current tile is processed
@@ -350,7 +370,7 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
   while (tile < T) {
     int next = 0;
     if (lane == 0) next = atomicAdd(tiles_next, 1);
-    const int r = tile_forest(a, q, s.off, tile, lane);
+    const int r = tile_forest(ta, q, s.off, tile, lane);
     const int cur = tile;
     tile = __shfl_sync(0xffffffffu, next, 0);
     if (r >= 0) {
