@@ -1,12 +1,13 @@
-// lem_forest.cuh -- one thread block runs Algs 1-6 of Barnes (arXiv:1803.02977)
-// on a whole grid by itself, with block barriers only.  Used by the batched
-// form, where each block owns one realization at a time.
+// lem_forest.cuh -- one thread block runs Algs 3-6 of Barnes (arXiv:1803.02977)
+// on a set of trees of one grid by itself, with block barriers only.  The
+// batched form uses it for the trees of a realization that do not fit a
+// warp's queue (lem_tiles.cuh).
 //
-// The queue of a grid lives in global memory in breadth-first order: level 0
-// (cells without receiver) first, then each level's donors in the order of
-// their receivers, each entry with its donor mask (pqm), receiver code (pqk)
-// and the position of its first donor (pqf).  Accumulation then runs in
-// queue order on a queue-ordered count array; erosion gathers elevations.
+// The queue lives in global memory in breadth-first order: level 0 (the
+// trees' roots, given) first, then each level's donors in the order of their
+// receivers, each entry with its donor mask (pqm), receiver code (pqk) and
+// the position of its first donor (pqf).  Accumulation then runs in queue
+// order on a queue-ordered count array; erosion gathers elevations.
 #pragma once
 
 #include "lem_step_kernel.cuh"
@@ -36,82 +37,7 @@ struct ForestGrid {
   float Udt;       // U*dt, rounded once to float
 };
 
-// Algs 1-2 and level 0 of Alg 3 over the whole grid: receiver codes, donor
-// masks, and the cells without receiver (ascending) as queue level 0.
-// Returns n0.  Each warp owns one contiguous range of cells.
-template <int BD, int PI>
-__device__ int forest_receivers(const ForestGrid& g, ForestSmem<BD, PI>& s) {
-  constexpr int W = BD / 32;
-  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  const int nx = g.nx, ny = g.ny, N = g.N;
-  const int wchunk = ((N + W - 1) / W + 31) & ~31;
-  const int w0 = min(N, w * wchunk), w1 = min(N, w0 + wchunk);
-  int wcnt = 0;
-  {
-    int x = w0 + lane, y = x / nx;
-    x -= y * nx;
-    for (int base = w0; base < w1; base += 32) {
-      const int c = base + lane;
-      int cd = kEdge;
-      if (c < w1) {
-        const bool perim = (x == 0 || y == 0 || x == nx - 1 || y == ny - 1);
-        cd = perim ? kEdge : receiver_of(g.h, c, nx);
-        g.code[c] = (uint8_t)cd;
-      }
-      wcnt += __popc(__ballot_sync(0xffffffffu, c < w1 && no_receiver(cd)));
-      x += 32;
-      while (x >= nx) {
-        x -= nx;
-        ++y;
-      }
-    }
-  }
-  if (lane == 0) s.wcount[w] = wcnt;
-  __syncthreads();
-  if (t == 0) {
-    int acc = 0;
-    for (int i = 0; i < W; ++i) {
-      s.wbase[i] = acc;
-      acc += s.wcount[i];
-    }
-    s.chunk_total = acc;
-  }
-  __syncthreads();
-  const int n0 = s.chunk_total;
-  {
-    int x = w0 + lane, y = x / nx;
-    x -= y * nx;
-    int run = s.wbase[w];
-    for (int base = w0; base < w1; base += 32) {
-      const int c = base + lane;
-      bool f = false;
-      int msk = 0, cd = kEdge;
-      if (c < w1) {
-        msk = donor_mask(g.code, c, x, y, nx, ny);
-        g.mask[c] = (uint8_t)msk;
-        cd = g.code[c];
-        f = no_receiver(cd);
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, f);
-      if (f) {
-        const int pos = run + __popc(bal & ((1u << lane) - 1u));
-        g.pq[pos] = c;
-        g.pqm[pos] = (uint8_t)msk;
-        g.pqk[pos] = (uint8_t)cd;
-      }
-      run += __popc(bal);
-      x += 32;
-      while (x >= nx) {
-        x -= nx;
-        ++y;
-      }
-    }
-  }
-  __syncthreads();
-  return n0;
-}
-
-// Alg 3: expand levels from level 0 = [0, n0).  Entries of a round are taken
+// Alg 3: expand levels from level 0 = [0, n0) (pq with pqm and pqk filled).  Entries of a round are taken
 // PI per thread (strided, so the loads coalesce) and emitted in parent order.
 // Returns the number of levels PL; plev[0..PL] holds the offsets.
 template <int BD, int PI>

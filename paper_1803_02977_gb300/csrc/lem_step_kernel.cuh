@@ -2,27 +2,20 @@
 // per-timestep method of Barnes (arXiv:1803.02977), Section "The Algorithm",
 // Algorithms 1-6, on one GB300.
 //
-// One launch covers any subset of the stages (phase bits) for nsteps steps.
-//
-// Receivers and donor masks (Algs 1-2) are grid-wide stencils; each block
-// owns a contiguous chunk of cells and each warp a contiguous sub-chunk, so
-// the cells without receiver (level 0 of Alg 3) are compacted in ascending
-// address order with warp ballots and one block-level prefix.
-//
-// Algs 3-6 then run in one of two forms:
-//  * block-private (lem_step): block b expands the breadth-first levels of
-//    the trees rooted at its own level-0 cells into a private queue, then
-//    accumulates (Alg 4) and erodes (Algs 5-6) exactly those trees.  Every
-//    donor of a cell lies in the same tree, so levels are separated by block
-//    barriers only -- the paper's private per-thread queues ("Independent
-//    Parallelism", RB+PQ) at the granularity of a thread block.  A block whose
-//    forest outgrows its queue share sets a flag and the whole step falls back
-//    to the device-wide form.
-//  * device-wide (stage-by-stage calls, and the fallback): one breadth-first
-//    queue for the whole grid, each level separated by a bounded grid barrier
-//    (the paper's "for-parallel" level loops), with runs of narrow levels
-//    handled by block 0 alone.  This form also produces the exported Queue and
-//    Levels in the oracle's breadth-first order.
+// One launch covers nsteps steps of one of two forms (phase bits):
+//  * tiered (lem_step, kPhTiles): Algs 1-2 as a TMA-staged register stencil
+//    over strips of the grid (phase_codes), a grid barrier, then Algs 3-6 on
+//    warp-private tile forests in shared memory (lem_tiles.cuh) -- the
+//    paper's private queues ("Independent Parallelism", RB+PQ) at warp
+//    granularity -- with a block-private tier (private_forest) and a
+//    device-wide tier for trees that do not fit, and a second grid barrier.
+//  * device-wide (stage-by-stage calls, step mode 1, and the device tier):
+//    Algs 1-2 with the cells without receiver compacted in ascending address
+//    order (phase_receivers), then one breadth-first queue for the whole grid
+//    with each level separated by a bounded grid barrier (the paper's
+//    "for-parallel" level loops) and runs of narrow levels handled by block 0
+//    alone.  This form produces the exported Queue and Levels in the
+//    oracle's breadth-first order.
 //
 // Data layout (all in HBM, row-major grid order unless stated):
 //   h      elevations (double or float), caller owned, updated in place
@@ -34,10 +27,11 @@
 //   cnt    i32 or i64 cell counts (Alg 4's A in units of cells)
 //
 // FP64 on GB300 runs at about 1/70 of the FP32 rate, so the FP64 work per
-// cell is kept small: receivers compare elevations through their bit
-// patterns and evaluate only the two candidate slopes in FP64 (exact, see
-// receiver_code), and erosion uses the increment form of the implicit update
-// with a tabulated F/(1+F) instead of a division (see erode_value).
+// cell is kept small: receivers decide from the elevations' high words or
+// bit patterns with FP32 slope margins and evaluate slopes in FP64 only for
+// near ties (exact, see receiver_code_vals), and erosion uses the increment
+// form of the implicit update with a tabulated F/(1+F) instead of a
+// division (see erode_value).
 #pragma once
 
 #include "lem_device.cuh"
