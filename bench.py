@@ -527,39 +527,44 @@ def measure_adjoint(lem, dev, nsteps=50, ckpt=10):
             "gradient_cell_steps_per_s": w.nx * w.ny * nsteps / el}
 
 
-def traced_step(lem, mdl, flush):
-    """One tiered step with device-side tracing, as seen by block 0: the
-    microseconds between consecutive trace points, grouped by what ended
-    them (block 0's own work, or the wait at a device-wide barrier)."""
+def traced_step(lem, mdl, flush, nsteps=3):
+    """Device-side trace of one launch of nsteps tiered steps, as seen by
+    block 0: the microseconds between consecutive trace points, grouped by
+    what ended them (block 0's own work, or the wait at a device-wide
+    barrier).  The first step of a launch includes the launch itself (blocks
+    starting on their SMs); later steps show the kernel in steady state."""
     lem.lem_trace_enable(mdl.ctx, 1 << 16)
     flush.zero_()
-    mdl.step(2)  # the second step's start marks the end of the first
+    mdl.step(nsteps)
     tr = lem.lem_trace_read(mdl.ctx, 1 << 16)
     lem.lem_trace_enable(mdl.ctx, 0)
-    starts = [i for i, e in enumerate(tr) if e[1] == "start"]
-    if len(starts) >= 2:
-        tr = tr[:starts[1] + 1]
-    if len(tr) < 2:
+    starts = [i for i, e in enumerate(tr) if e[1] == "start"] + [len(tr) - 1]
+    steps = []
+    for k in range(len(starts) - 1):
+        seg = tr[starts[k]:starts[k + 1] + 1]
+        if len(seg) < 2:
+            continue
+        out = {"codes": 0.0, "codes_wait": 0.0, "tiles_warp": 0.0, "tiles_block": 0.0,
+               "tiles_wait": 0.0, "device_tier": 0.0}
+        for (t0, _, _), (t1, ph, lvl) in zip(seg[:-1], seg[1:]):
+            us = (t1 - t0) / 1e3
+            if ph == "block0_done":
+                key = {1: "codes", 4: "tiles_warp"}.get(lvl, "tiles_block")
+            elif ph == "receivers":
+                key = "codes_wait"
+            elif ph == "tiles_end":
+                key = "tiles_wait"
+            else:
+                key = "device_tier"
+            out[key] += us
+        steps.append({"us": out, "total_us": (seg[-1][0] - seg[0][0]) / 1e3})
+    if not steps:
         return None
-    out = {"codes": 0.0, "codes_wait": 0.0, "tiles_warp": 0.0, "tiles_block": 0.0,
-           "tiles_wait": 0.0, "device_tier": 0.0}
-    device_levels = 0
-    for (t0, _, _), (t1, ph, lvl) in zip(tr[:-1], tr[1:]):
-        us = (t1 - t0) / 1e3
-        if ph == "block0_done":
-            key = {1: "codes", 4: "tiles_warp"}.get(lvl, "tiles_block")
-        elif ph == "receivers":
-            key = "codes_wait"
-        elif ph == "tiles_end":
-            key = "tiles_wait"
-        else:
-            key = "device_tier"
-            device_levels += ph.endswith("_wide") or ph.endswith("_narrow")
-        out[key] += us
     raw = [[ph, lvl, round((t1 - t0) / 1e3, 2)]
            for (t0, _, _), (t1, ph, lvl) in zip(tr[:-1], tr[1:])][:64]
-    return {"us": out, "total_us": (tr[-1][0] - tr[0][0]) / 1e3, "segments": len(tr) - 1,
-            "device_tier_barrier_runs": device_levels, "raw": raw}
+    return {"us": steps[0]["us"], "total_us": steps[0]["total_us"],
+            "steady_state_step": steps[-1] if len(steps) > 1 else None,
+            "steps_in_launch": nsteps, "raw": raw}
 
 
 def kernel_source_hash():

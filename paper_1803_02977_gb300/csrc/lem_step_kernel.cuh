@@ -722,6 +722,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, 
       "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// Hint the TMA unit to bring the box at (x, y) into L2 (no shared memory
+// involved, nothing to wait for).
+__device__ __forceinline__ void tma_prefetch_2d(const void* tmap, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(tmap),
+               "r"(x), "r"(y)
+               : "memory");
+}
+
 // Wait for phase `parity` of bar, bounded by the context's wait limit.
 // Returns false (with kErrTimeout recorded) if the limit ran out or another
 // block recorded an error.
@@ -858,6 +866,11 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
         fence_proxy_async_smem();  // the previous strip's reads of S come first
         mbar_expect_tx(bar, (unsigned)(kStageRows * kStageCols * sizeof(HT)));
         tma_load_2d(S, &a.tmap, xb, yb, bar);
+        if (next < u1) {
+          // the warp's next strip, into L2 while this one is computed
+          const int nsy = next / nsx, nsx0 = (next - nsy * nsx) * kStripOut;
+          tma_prefetch_2d(&a.tmap, (nsx0 - 2) & ~(kAlign - 1), nsy * kStripRows - 2);
+        }
       }
       ok = __all_sync(0xffffffffu, mbar_wait(bar, parity, st));
       parity ^= 1u;
@@ -871,6 +884,7 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
   }
   __syncwarp();
   if (tma && lane == 0 && ok) mbar_inval(bar);
+  __syncthreads();  // the trace marks the whole block's end of Alg 1
   trace_point(a.st, kTrLocal + 1);
   if (!grid_barrier(a.st, gridDim.x)) return false;
   trace_point(a.st, kTrCodes);
