@@ -749,15 +749,20 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   return true;
 }
 
-// Donor mask from packed codes: byte 0 = row above, 1 = own row, 2 = row
-// below, of the left lane (cl), this lane (cw) and the right lane (cr).
-__device__ __forceinline__ int mask_from_packed(unsigned cl, unsigned cw, unsigned cr) {
-  const unsigned eL = __vcmpeq4(cl, 0xEE020407u);  // NW: 7, W: 4, SW: 2
-  const unsigned eC = __vcmpeq4(cw, 0xEE01EE06u);  // N: 6, S: 1
-  const unsigned eR = __vcmpeq4(cr, 0xEE000305u);  // NE: 5, E: 3, SE: 0
-  return (int)((eL & 1u) | ((eC & 1u) << 1) | ((eR & 1u) << 2) | (((eL >> 8) & 1u) << 3) |
-               (((eR >> 8) & 1u) << 4) | (((eL >> 16) & 1u) << 5) | (((eC >> 16) & 1u) << 6) |
-               (((eR >> 16) & 1u) << 7));
+// A cell's receiver code as a one-hot byte: bit d set when it drains to its
+// neighbour d, zero without receiver (codes 8, 9) or outside the grid (0xFF).
+__device__ __forceinline__ unsigned pointer_bits(int cd) { return cd < 8 ? 1u << cd : 0u; }
+
+// Donor mask from packed pointer bytes (byte 0 = row above, 1 = own row, 2 =
+// row below) of the left lane (pl), this lane (pw) and the right lane (pr).
+// Neighbour k drains into the cell iff its byte has bit 7-k: NW bit 7, N 6,
+// NE 5 above; W 4, E 3 beside; SW 2, S 1, SE 0 below.  Those eight bits are
+// disjoint, so they fold into one byte t with bit 7-k for neighbour k, and
+// the mask (bit k for neighbour k) is t bit-reversed.
+__device__ __forceinline__ int mask_from_pointers(unsigned pl, unsigned pw, unsigned pr) {
+  const unsigned v = (pl & 0x041080u) | (pw & 0x020040u) | (pr & 0x010820u);
+  const unsigned t = (v | (v >> 8) | (v >> 16)) & 0xFFu;
+  return (int)(__brev(t) >> 24);
 }
 
 // Algs 1-2 on one staged strip: S holds rows y0-2 .. y0+kStripRows+1 and
@@ -776,42 +781,42 @@ __device__ __forceinline__ void codes_strip(const HT* S, uint8_t* code, uint8_t*
   const bool xperim = x == 0 || x == nx - 1;
   const bool own = lane >= 1 && lane <= kStripOut && xin;
   const int sc = x - xb;  // staged column of this lane's cell, 1..35
-    HT ul = HT(0), uc = HT(0), ur = HT(0), ml = HT(0), mc = HT(0), mr = HT(0);
+  HT ul = HT(0), uc = HT(0), ur = HT(0), ml = HT(0), mc = HT(0), mr = HT(0);
+  if (!frozen) {
+    ul = S[sc - 1];
+    uc = S[sc];
+    ur = S[sc + 1];
+    ml = S[kStageCols + sc - 1];
+    mc = S[kStageCols + sc];
+    mr = S[kStageCols + sc + 1];
+  }
+  long long at = (long long)(y0 - 1) * nx + x;  // this lane's cell in row y
+  unsigned pw = 0;  // pointer bytes of rows y-2, y-1, y in bytes 0, 1, 2
+  for (int y = y0 - 1; y <= y1; ++y, at += nx) {
+    int cd = 0xFF;
+    const bool in = xin && y >= 0 && y < ny;
     if (!frozen) {
-      ul = S[sc - 1];
-      uc = S[sc];
-      ur = S[sc + 1];
-      ml = S[kStageCols + sc - 1];
-      mc = S[kStageCols + sc];
-      mr = S[kStageCols + sc + 1];
-    }
-    unsigned cw = 0xFFFFFFFFu;  // codes of rows y-2, y-1, y in bytes 0, 1, 2
-    for (int y = y0 - 1; y <= y1; ++y) {
-      int cd = 0xFF;
-      const bool yin = y >= 0 && y < ny;
-      if (!frozen) {
-        const HT* Sd = S + (y + 1 - yb) * kStageCols + sc;
-        const HT dl = Sd[-1], dc = Sd[0], dr = Sd[1];
-        if (xin && yin) {
-          if (xperim || y == 0 || y == ny - 1) {
-            cd = kEdge;
-          } else {
-            const HT v[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
-            cd = receiver_from(mc, v);
-          }
-          if (own && y >= y0 && y < y1) code[(size_t)y * nx + x] = (uint8_t)cd;
+      const HT* Sd = S + (y + 1 - yb) * kStageCols + sc;
+      const HT dl = Sd[-1], dc = Sd[0], dr = Sd[1];
+      if (in) {
+        if (xperim || y == 0 || y == ny - 1) {
+          cd = kEdge;
+        } else {
+          const HT v[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
+          cd = receiver_from(mc, v);
         }
-        ul = ml; uc = mc; ur = mr;
-        ml = dl; mc = dc; mr = dr;
-      } else if (xin && yin) {
-        cd = code[(size_t)y * nx + x];
+        if (own && y >= y0 && y < y1) code[at] = (uint8_t)cd;
       }
-      cw = ((cw >> 8) & 0xFFFFu) | ((unsigned)cd << 16);
-      const unsigned cl = __shfl_up_sync(0xffffffffu, cw, 1);
-      const unsigned cr = __shfl_down_sync(0xffffffffu, cw, 1);
-      if (own && y - 1 >= y0 && y - 1 < y1)
-        mask[(size_t)(y - 1) * nx + x] = (uint8_t)mask_from_packed(cl, cw, cr);
+      ul = ml; uc = mc; ur = mr;
+      ml = dl; mc = dc; mr = dr;
+    } else if (in) {
+      cd = code[at];
     }
+    pw = ((pw >> 8) & 0xFFFFu) | (pointer_bits(cd) << 16);
+    const unsigned pl = __shfl_up_sync(0xffffffffu, pw, 1);
+    const unsigned pr = __shfl_down_sync(0xffffffffu, pw, 1);
+    if (own && y > y0 && y <= y1) mask[at - nx] = (uint8_t)mask_from_pointers(pl, pw, pr);
+  }
 }
 
 template <typename HT, typename CT>
