@@ -183,11 +183,7 @@ __device__ __forceinline__ bool no_rounding_merge(typename Bits<HT>::U m, typena
 // are compared in FP32 from the high words (relative error below 2^-19
 // each), deciding when they differ by more than 2^-16 of h_c plus 2^-16 of
 // the slopes.  Returns -1 when any of this does not hold.
-__device__ __forceinline__ int receiver_code_hi(const double hcd, const double* v) {
-  const unsigned hc = (unsigned)__double2hiint(hcd);
-  unsigned x[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) x[k] = (unsigned)__double2hiint(v[k]);
+__device__ __forceinline__ int receiver_code_hi_words(const unsigned hc, const unsigned* x) {
   unsigned worst = hc;
 #pragma unroll
   for (int k = 0; k < 8; ++k) worst = max(worst, x[k]);
@@ -218,6 +214,13 @@ __device__ __forceinline__ int receiver_code_hi(const double hcd, const double* 
                          (hasC && hasD && !cWins && !dWins);
   const int code = !hasC ? (hasD ? kD : kSink) : (!hasD ? kC : (cWins ? kC : kD));
   return undecided ? -1 : code;
+}
+
+__device__ __forceinline__ int receiver_code_hi(const double hcd, const double* v) {
+  unsigned x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = (unsigned)__double2hiint(v[k]);
+  return receiver_code_hi_words((unsigned)__double2hiint(hcd), x);
 }
 
 template <typename HT>
@@ -771,6 +774,51 @@ __device__ __forceinline__ int mask_from_pointers(unsigned pl, unsigned pw, unsi
 // registers and writes the codes and masks of the owned cells (lanes 1 ..
 // kStripOut, rows y0 .. y0+kStripRows-1, inside the grid).  With frozen
 // receivers the codes are read instead of computed.
+// codes_strip for FP64 elevations: the register window holds only the high
+// words of the values (receiver_code_hi_words decides from them alone); a
+// cell it leaves undecided reloads its nine doubles from the staged strip
+// for the exact comparison.
+__device__ __forceinline__ void codes_strip_f64(const double* S, uint8_t* code, uint8_t* mask,
+                                                int nx, int ny, int x, int y0, int y1, bool xin,
+                                                bool xperim, bool own, int sc) {
+  const int yb = y0 - 2;
+  // high word of staged element (row r, column col)
+  auto hw = [&](int r, int col) -> unsigned {
+    return reinterpret_cast<const unsigned*>(S + r * kStageCols + col)[1];
+  };
+  unsigned ul = hw(0, sc - 1), uc = hw(0, sc), ur = hw(0, sc + 1);
+  unsigned ml = hw(1, sc - 1), mc = hw(1, sc), mr = hw(1, sc + 1);
+  long long at = (long long)(y0 - 1) * nx + x;
+  unsigned pw = 0;
+  for (int y = y0 - 1; y <= y1; ++y, at += nx) {
+    const int r = y + 1 - yb;  // staged row below the cell
+    const unsigned dl = hw(r, sc - 1), dc = hw(r, sc), dr = hw(r, sc + 1);
+    int cd = 0xFF;
+    if (xin && y >= 0 && y < ny) {
+      if (xperim || y == 0 || y == ny - 1) {
+        cd = kEdge;
+      } else {
+        const unsigned xs[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
+        cd = receiver_code_hi_words(mc, xs);
+        if (cd < 0) {
+          const double* up = S + (r - 2) * kStageCols + sc;
+          const double* md = up + kStageCols;
+          const double* dn = md + kStageCols;
+          const double v[8] = {up[-1], up[0], up[1], md[-1], md[1], dn[-1], dn[0], dn[1]};
+          cd = receiver_code_vals(md[0], v);
+        }
+      }
+      if (own && y >= y0 && y < y1) code[at] = (uint8_t)cd;
+    }
+    ul = ml; uc = mc; ur = mr;
+    ml = dl; mc = dc; mr = dr;
+    pw = ((pw >> 8) & 0xFFFFu) | (pointer_bits(cd) << 16);
+    const unsigned pl = __shfl_up_sync(0xffffffffu, pw, 1);
+    const unsigned pr = __shfl_down_sync(0xffffffffu, pw, 1);
+    if (own && y > y0 && y <= y1) mask[at - nx] = (uint8_t)mask_from_pointers(pl, pw, pr);
+  }
+}
+
 template <typename HT>
 __device__ __forceinline__ void codes_strip(const HT* S, uint8_t* code, uint8_t* mask, int nx,
                                             int ny, int x0, int y0, int xb, bool frozen,
@@ -781,6 +829,13 @@ __device__ __forceinline__ void codes_strip(const HT* S, uint8_t* code, uint8_t*
   const bool xperim = x == 0 || x == nx - 1;
   const bool own = lane >= 1 && lane <= kStripOut && xin;
   const int sc = x - xb;  // staged column of this lane's cell, 1..35
+  if constexpr (sizeof(HT) == 8) {
+    if (!frozen) {
+      codes_strip_f64(reinterpret_cast<const double*>(S), code, mask, nx, ny, x, y0, y1, xin,
+                      xperim, own, sc);
+      return;
+    }
+  }
   HT ul = HT(0), uc = HT(0), ur = HT(0), ml = HT(0), mc = HT(0), mr = HT(0);
   if (!frozen) {
     ul = S[sc - 1];
