@@ -11,6 +11,18 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
+def _funnel(nx, ny, seed, cx, cy, r):
+    # one basin of ~pi*r^2 cells around a single pit in a noise field: too
+    # many for a warp's queue, so its tile is finished by the block-wide forest
+    h = 100.0 + synth.uniform01(seed, nx * ny).reshape(ny, nx)
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    d = np.hypot(x - cx, y - cy)
+    inside = d <= r
+    h[inside] = 50.0 + d[inside] + 0.001 * h[inside]
+    h[0, :] = h[-1, :] = h[:, 0] = h[:, -1] = 0.0
+    return h
+
+
 def _realizations(R=11, seed=4):
     u = synth.uniform01(seed, 4 * R).reshape(R, 4)
     shapes = [(int(3 + u[r, 0] * 300), int(3 + u[r, 1] * 260)) for r in range(R)]
@@ -19,17 +31,20 @@ def _realizations(R=11, seed=4):
     Ks = [float(10 ** (-6 + 2 * u[r, 2])) for r in range(R)]
     ms = [float(0.4 + 0.2 * u[r, 3]) for r in range(R)]
     surfaces = [synth.noise_surface(nx, ny, 1000 + r) for r, (nx, ny) in enumerate(shapes)]
+    surfaces[2] = _funnel(97, 83, 1002, cx=40, cy=41, r=16.0)
     return surfaces, Ks, ms
 
 
 def _singles(surfaces, Ks, ms, steps):
     from paper_1803_02977_gb300 import lem
     out = []
-    for s, K, m in zip(surfaces, Ks, ms):
+    for i, (s, K, m) in enumerate(zip(surfaces, Ks, ms)):
         h = torch.tensor(s.astype(np.float32), device="cuda:0")
         mdl = lem.Model(h, dx=100.0, K=K, m=m, U=1e-3, dt=1000.0)
         mdl.step(steps)
         mdl.sync()
+        if i == 2:  # the funnel exercises the fallback tier in both paths
+            assert lem.lem_tier_stats(mdl.ctx)[1] > 0
         out.append(h.cpu().numpy())
         mdl.close()
     return out

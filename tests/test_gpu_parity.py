@@ -177,6 +177,8 @@ def test_step_matches_oracle_per_step():
 # (name, grid, which lem_step tiers must run; None: not pinned)
 STEP_CASES = [
     ("noise_256", lambda: synth.noise_surface(256, 256, 1), "tiles"),
+    # row pitch not a multiple of 16 bytes: strips staged element-wise, not by TMA
+    ("noise_odd_257x190", lambda: synth.noise_surface(257, 190, 4), "tiles"),
     ("noise_tilt_700x500", lambda: synth.noise_surface(700, 500, 3, south_tilt=1e-4), "tiles"),
     ("int_300x300", lambda: _int_grid(300, 300, 9, levels=12), None),
     # one chain of ~300 cells per row, rooted on the west edge: too deep for a
