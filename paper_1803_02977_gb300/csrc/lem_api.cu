@@ -175,6 +175,7 @@ StepArgs<HT, CT> make_args(lem_ctx* c, int phases, int nsteps) {
   a.pcap = c->pcap;
   a.tiles_x = (c->p.nx + kTileW - 1) / kTileW;
   a.ntiles = a.tiles_x * ((c->p.ny + tile_h<HT>() - 1) / tile_h<HT>());
+  a.strip_rows = pick_strip_rows<HT>(c->p.nx, c->p.ny, c->grid * kWarps);
   a.has_tmap = c->tmap_ok ? 1 : 0;
   a.tmap = c->tmap;
   a.Udt = c->p.U * c->p.dt;
@@ -228,7 +229,7 @@ int read_status(lem_ctx* c, int* nlevels) {
 bool is_finite(double v) { return std::isfinite(v); }
 
 // Encode the TMA descriptor of the bound elevations (2-D: nx x ny elements,
-// box kStageCols x kStageRows, zero fill outside) into c->tmap; every launch
+// box kStageCols x (strip rows + 4), zero fill outside) into c->tmap; every launch
 // passes it in its kernel parameter.  Leaves c->tmap_ok false -- the step kernel then
 // stages strips with per-element copies -- when TMA cannot describe h (row
 // pitch or base not a multiple of 16 bytes) or the driver lacks the encoder.
@@ -259,7 +260,9 @@ int encode_tmap(lem_ctx* c) {
   std::memset(&m, 0, sizeof(m));
   const cuuint64_t dims[2] = {(cuuint64_t)c->p.nx, (cuuint64_t)c->p.ny};
   const cuuint64_t strides[1] = {(cuuint64_t)pitch};
-  const cuuint32_t box[2] = {(cuuint32_t)kStageCols, (cuuint32_t)kStageRows};
+  const int rows = esz == 8 ? pick_strip_rows<double>(c->p.nx, c->p.ny, c->grid * kWarps)
+                            : pick_strip_rows<float>(c->p.nx, c->p.ny, c->grid * kWarps);
+  const cuuint32_t box[2] = {(cuuint32_t)kStageCols, (cuuint32_t)(rows + 4)};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode(&m, esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,

@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(BD) lem_batch_kernel(BatchArgs a) {
     ta.ero.Udt_f = g.Udt;
     const int ntiles = ta.tiles_x * ((g.ny + TH - 1) / TH);
     const int nsx = (g.nx + kStripOut - 1) / kStripOut;
-    const int units = nsx * ((g.ny + kStripRows - 1) / kStripRows);
+    const int rows = pick_strip_rows<float>(g.nx, g.ny, BD / 32);
+    const int units = nsx * ((g.ny + rows - 1) / rows);
     if (t < 8) s_off[t] = nbr_off(t, g.nx);
     for (int step = 0; step < a.nsteps; ++step) {
       // Algs 1-2: the realization's strips, claimed by the block's warps
@@ -141,10 +142,10 @@ __global__ void __launch_bounds__(BD) lem_batch_kernel(BatchArgs a) {
         u = __shfl_sync(0xffffffffu, u, 0);
         if (u >= units) break;
         const int sy = u / nsx, sx = u - sy * nsx;
-        const int x0 = sx * kStripOut, y0 = sy * kStripRows;
+        const int x0 = sx * kStripOut, y0 = sy * rows;
         const int xb = (x0 - 2) & ~3;
-        stage_strip(g.h, g.nx, g.ny, xb, y0 - 2, S, lane);
-        codes_strip(S, g.code, g.mask, g.nx, g.ny, x0, y0, xb, false, lane);
+        stage_strip(g.h, g.nx, g.ny, xb, y0 - 2, rows + 4, S, lane);
+        codes_strip(S, g.code, g.mask, g.nx, g.ny, x0, y0, rows, xb, false, lane);
         __syncwarp();
       }
       __syncthreads();

@@ -166,6 +166,7 @@ extern "C" LEM_API int lem_step_noalloc(int nx, int ny, double* dev_h, double dx
   a.partial = reinterpret_cast<int*>(base + kOffPartial);
   a.tiles_x = (nx + kTileW - 1) / kTileW;
   a.ntiles = a.tiles_x * ((ny + tile_h<double>() - 1) / tile_h<double>());
+  a.strip_rows = pick_strip_rows<double>(nx, ny, grid * kWarps);
   a.has_tmap = 0;  // strips are staged with per-element asynchronous copies
   a.phases = kPhTiles;
   a.nsteps = nsteps;

@@ -66,8 +66,9 @@ struct StepArgs {
   CT* cntq;             // cell count of each private-queue entry (queue order)
   int pcap;             // entries per block in pq
   int tiles_x, ntiles;  // warp-tier tiles per row, in total
+  int strip_rows;       // owned rows per strip of the codes pass (pick_strip_rows)
   int has_tmap;         // tmap describes h (else strips are staged element-wise)
-  TmaDesc tmap;         // TMA descriptor of h: 2-D, kStageCols x kStageRows box
+  TmaDesc tmap;         // TMA descriptor of h: 2-D box of kStageCols x (strip_rows + 4)
   CT* cnt;
   const double2* Ftab;  // {F, F/(1+F)} for counts < kTableN: [0,N) cardinal, [N,2N) diagonal
   const float* gtab;    // F/(1+F) rounded to float, same layout
@@ -644,7 +645,7 @@ __device__ __forceinline__ int codes_sweep(const StepArgs<HT, CT>& a, int w0, in
 }
 
 // Algs 1-2 for the tiered step.  A warp owns a strip of kStripOut columns
-// and kStripRows rows at a time.  It first stages the elevations the strip
+// and strip_rows() rows at a time.  It first stages the elevations the strip
 // needs (two rows and columns of halo on each side) into its slice of shared
 // memory with asynchronous copies, all in flight at once; then lane l walks
 // down column x0 - 1 + l (lanes 0 and 31 are halo columns) with a 3x3 window
@@ -654,8 +655,25 @@ __device__ __forceinline__ int codes_sweep(const StepArgs<HT, CT>& a, int w0, in
 // Cells outside the grid count as code 0xFF (no receiver anywhere), which
 // leaves the perimeter cells' masks exact.
 constexpr int kStripOut = 30;                // owned columns per strip (lanes 1..30)
-constexpr int kStripRows = 16;               // owned rows per strip
-constexpr int kStageRows = kStripRows + 4;   // staged rows: two of halo each side
+// owned rows per strip, at most: 32 with FP32 elevations, 16 with FP64
+// (whose staged strip must also fit a warp's slice of shared memory).  A
+// pass takes 16-row strips when the taller ones would leave fewer than two
+// per warp (pick_strip_rows).
+template <typename HT>
+__host__ __device__ constexpr int strip_rows() {
+  return sizeof(HT) == 4 ? 32 : 16;
+}
+// staged rows at most: two of halo on each side
+template <typename HT>
+__host__ __device__ constexpr int stage_rows() {
+  return strip_rows<HT>() + 4;
+}
+template <typename HT>
+__host__ __device__ __forceinline__ int pick_strip_rows(int nx, int ny, int warps) {
+  constexpr int R = strip_rows<HT>();
+  const long long tall = (long long)((nx + kStripOut - 1) / kStripOut) * ((ny + R - 1) / R);
+  return (R > 16 && tall < 2LL * warps) ? 16 : R;
+}
 constexpr int kStageCols = 36;               // staged columns (16-byte aligned start)
 
 template <typename HT>
@@ -666,12 +684,12 @@ __device__ __forceinline__ void cp_async_elem(HT* dst, const HT* src, bool in) {
                : "memory");
 }
 
-// Stage rows [yb, yb + kStageRows) x columns [xb, xb + kStageCols) of h into
+// Stage rows [yb, yb + rows) x columns [xb, xb + kStageCols) of h into
 // S (row-major); positions outside the grid are zero-filled.
 template <typename HT>
-__device__ __forceinline__ void stage_strip(const HT* h, int nx, int ny, int xb, int yb, HT* S,
-                                            int lane) {
-  for (int i = lane; i < kStageRows * kStageCols; i += 32) {
+__device__ __forceinline__ void stage_strip(const HT* h, int nx, int ny, int xb, int yb, int rows,
+                                            HT* S, int lane) {
+  for (int i = lane; i < rows * kStageCols; i += 32) {
     const int r = i / kStageCols, col = i - r * kStageCols;
     const int x = xb + col, y = yb + r;
     const bool in = x >= 0 && x < nx && y >= 0 && y < ny;
@@ -768,11 +786,11 @@ __device__ __forceinline__ int mask_from_pointers(unsigned pl, unsigned pw, unsi
   return (int)(__brev(t) >> 24);
 }
 
-// Algs 1-2 on one staged strip: S holds rows y0-2 .. y0+kStripRows+1 and
+// Algs 1-2 on one staged strip: S holds rows y0-2 .. y0+rows+1 and
 // columns xb .. xb+kStageCols-1 of the elevations (zero outside the grid).
 // Lane l walks column x0 - 1 + l down the strip with a 3 x 3 window in
 // registers and writes the codes and masks of the owned cells (lanes 1 ..
-// kStripOut, rows y0 .. y0+kStripRows-1, inside the grid).  With frozen
+// kStripOut, rows y0 .. y0+rows-1, inside the grid).  With frozen
 // receivers the codes are read instead of computed.
 // codes_strip for FP64 elevations: the register window holds only the high
 // words of the values (receiver_code_hi_words decides from them alone); a
@@ -821,10 +839,10 @@ __device__ __forceinline__ void codes_strip_f64(const double* S, uint8_t* code, 
 
 template <typename HT>
 __device__ __forceinline__ void codes_strip(const HT* S, uint8_t* code, uint8_t* mask, int nx,
-                                            int ny, int x0, int y0, int xb, bool frozen,
+                                            int ny, int x0, int y0, int rows, int xb, bool frozen,
                                             int lane) {
   const int x = x0 - 1 + lane;  // this lane's column
-  const int y1 = min(ny, y0 + kStripRows), yb = y0 - 2;
+  const int y1 = min(ny, y0 + rows), yb = y0 - 2;
   const bool xin = x >= 0 && x < nx;
   const bool xperim = x == 0 || x == nx - 1;
   const bool own = lane >= 1 && lane <= kStripOut && xin;
@@ -876,8 +894,9 @@ __device__ __forceinline__ void codes_strip(const HT* S, uint8_t* code, uint8_t*
 
 template <typename HT, typename CT>
 __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
-  static_assert(kStageRows * kStageCols * sizeof(HT) + 16 <= kWarpBytes,
+  static_assert(stage_rows<HT>() * kStageCols * sizeof(HT) + 16 <= kWarpBytes,
                 "strip and barrier fit the warp slice");
+  const int kRows = a.strip_rows;
   constexpr int kAlign = 16 / (int)sizeof(HT);  // staged start: a 16-byte multiple
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
@@ -893,7 +912,7 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
   uint8_t* const mask = a.mask;
   DevState* const st = a.st;
   const int nsx = (nx + kStripOut - 1) / kStripOut;
-  const int units = nsx * ((ny + kStripRows - 1) / kStripRows);
+  const int units = nsx * ((ny + kRows - 1) / kRows);
   // each block takes an equal contiguous range of strips, its warps claim
   // them one at a time (the next claim issued before the current strip)
   __shared__ int s_next;
@@ -918,27 +937,27 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
     if (lane == 0) next = atomicAdd(&s_next, 1);
     const int sy = u / nsx, sx = u - sy * nsx;
     const int x0 = sx * kStripOut;  // first owned column
-    const int y0 = sy * kStripRows;
+    const int y0 = sy * kRows;
     // staged columns start at x0 - 2 rounded down to 16 bytes
     const int xb = (x0 - 2) & ~(kAlign - 1), yb = y0 - 2;
     if (tma) {
       if (lane == 0) {
         fence_proxy_async_smem();  // the previous strip's reads of S come first
-        mbar_expect_tx(bar, (unsigned)(kStageRows * kStageCols * sizeof(HT)));
+        mbar_expect_tx(bar, (unsigned)((kRows + 4) * kStageCols * sizeof(HT)));
         tma_load_2d(S, &a.tmap, xb, yb, bar);
         if (next < u1) {
           // the warp's next strip, into L2 while this one is computed
           const int nsy = next / nsx, nsx0 = (next - nsy * nsx) * kStripOut;
-          tma_prefetch_2d(&a.tmap, (nsx0 - 2) & ~(kAlign - 1), nsy * kStripRows - 2);
+          tma_prefetch_2d(&a.tmap, (nsx0 - 2) & ~(kAlign - 1), nsy * kRows - 2);
         }
       }
       ok = __all_sync(0xffffffffu, mbar_wait(bar, parity, st));
       parity ^= 1u;
       if (!ok) break;
     } else if (!frozen) {
-      stage_strip(h, nx, ny, xb, yb, S, lane);
+      stage_strip(h, nx, ny, xb, yb, kRows + 4, S, lane);
     }
-    codes_strip(S, code, mask, nx, ny, x0, y0, xb, frozen, lane);
+    codes_strip(S, code, mask, nx, ny, x0, y0, kRows, xb, frozen, lane);
     __syncwarp();  // S is restaged by the next unit
     u = __shfl_sync(0xffffffffu, next, 0);
   }
