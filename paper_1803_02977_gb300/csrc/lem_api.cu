@@ -278,6 +278,14 @@ int encode_tmap(lem_ctx* c) {
 
 }  // namespace
 
+// The step arguments of a context for its current binding, for the other
+// translation units' launches (the adjoint sweep).
+int lem_make_step_args(lem_ctx* c, StepArgs<double, int>* a) {
+  if (!c || !a || c->p.dtype != LEM_F64 || c->p.count_bits != 32) return LEM_EINVAL;
+  *a = make_args<double, int>(c, 0, 1);
+  return LEM_OK;
+}
+
 extern "C" {
 
 const char* lem_status_string(int s) {
