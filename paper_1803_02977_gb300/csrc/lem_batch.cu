@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(BD) lem_batch_kernel(BatchArgs a) {
         if (lane == 0) tile = atomicAdd(&s_next, 1);
         tile = __shfl_sync(0xffffffffu, tile, 0);
         if (tile >= ntiles) break;
-        if (tile_forest(ta, q, s_off, tile, lane) < 0 && lane == 0)
+        if (tile_forest(ta, q, s_off, tile_item(tile, 0), lane) < 0 && lane == 0)
           g.pqf[atomicAdd(&s_n_ovf, 1)] = tile;
       }
       __syncthreads();
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(BD) lem_batch_kernel(BatchArgs a) {
         // their roots as level 0 of the block-wide forest
         for (int i = w; i < nov; i += BD / 32) {
           int cd[TH], x, y0;
-          tile_codes<TH>(g.code, g.pqf[i], ta.tiles_x, g.nx, g.ny, lane, cd, &x, &y0);
+          tile_codes<TH>(g.code, g.pqf[i], 0, TH, ta.tiles_x, g.nx, g.ny, lane, cd, &x, &y0);
 #pragma unroll
           for (int rr = 0; rr < TH; ++rr) {
             const bool f = cd[rr] >= kSink;

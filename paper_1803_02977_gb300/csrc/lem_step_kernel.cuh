@@ -586,9 +586,9 @@ struct Shared {
   int wcount[kWarps];
   int chunk[kPItems * kWarps];  // per (slot, warp) donor totals, then offsets
   int chunk_total;
-  int n_ovf, n0;                // block tier: overflowed tiles, roots
+  int n_ovf, n0;                // block tier: overflowed work items, roots
   int off[8];                   // address offset of neighbour k
-  int ovf_tiles[kOvfCap];
+  int ovf_tiles[kOvfCap];       // overflowed work items (tile_item packing)
 };
 static_assert(kPItems * kWarps == 8 * 32, "one warp scans the chunk totals 8 per lane");
 

@@ -54,28 +54,45 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Level 0 of one tile as seen by lane `lane`: the row codes of its column.
-// Out-of-grid positions read as 0 (a cell with a receiver: never a root).
+// A unit of warp-tier work: the trees rooted in all rows of a tile, or in
+// one half of its rows (the last tiles of a step are split in two so that
+// the warps finish closer together).  Packed as tile << 2 | part, part 0 =
+// every row, 1 = rows [0, TH/2), 2 = rows [TH/2, TH).
+__device__ __forceinline__ int tile_item(int tile, int part) { return tile << 2 | part; }
 template <int TH>
-__device__ __forceinline__ void tile_codes(const uint8_t* code, int tile, int tiles_x, int nx,
-                                           int ny, int lane, int* cd, int* x, int* y0) {
+__device__ __forceinline__ void item_rows(int item, int* tile, int* rlo, int* rhi) {
+  const int part = item & 3;
+  *tile = item >> 2;
+  *rlo = part == 2 ? TH / 2 : 0;
+  *rhi = part == 1 ? TH / 2 : TH;
+}
+
+// Level 0 of one tile as seen by lane `lane`: the row codes of its column,
+// for rows [rlo, rhi).  Other rows and out-of-grid positions read as 0 (a
+// cell with a receiver: never a root).
+template <int TH>
+__device__ __forceinline__ void tile_codes(const uint8_t* code, int tile, int rlo, int rhi,
+                                           int tiles_x, int nx, int ny, int lane, int* cd, int* x,
+                                           int* y0) {
   const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
   *x = tx * kTileW + lane;
   *y0 = ty * TH;
 #pragma unroll
   for (int r = 0; r < TH; ++r) {
     const int y = *y0 + r;
-    cd[r] = (*x < nx && y < ny) ? code[(size_t)y * nx + *x] : 0;
+    cd[r] = (*x < nx && y < ny && r >= rlo && r < rhi) ? code[(size_t)y * nx + *x] : 0;
   }
 }
 
-// Append the roots of `tile` to the device tier's level 0 (queue[0, n)).
+// Append the roots of work item `item` to the device tier's level 0
+// (queue[0, n)).
 template <int TH>
 __device__ __forceinline__ void push_tile_roots_device(const uint8_t* code, int* queue,
-                                                       int* dev_roots, int tile, int tiles_x,
+                                                       int* dev_roots, int item, int tiles_x,
                                                        int nx, int ny, int lane) {
-  int cd[TH], x, y0;
-  tile_codes<TH>(code, tile, tiles_x, nx, ny, lane, cd, &x, &y0);
+  int cd[TH], x, y0, tile, rlo, rhi;
+  item_rows<TH>(item, &tile, &rlo, &rhi);
+  tile_codes<TH>(code, tile, rlo, rhi, tiles_x, nx, ny, lane, cd, &x, &y0);
 #pragma unroll
   for (int r = 0; r < TH; ++r) {
     const bool f = cd[r] >= kSink;
@@ -131,12 +148,12 @@ struct TileArgs {
   TileErode<HT> ero;
 };
 
-// Algs 3-6 on the trees rooted in `tile`, by one warp.  off[k] is the
-// address offset of neighbour k.  Returns the number of cells handled, or -1
-// if the forest does not fit (nothing was written).
+// Algs 3-6 on the trees rooted in work item `item` (tile_item), by one warp.
+// off[k] is the address offset of neighbour k.  Returns the number of cells
+// handled, or -1 if the forest does not fit (nothing was written).
 template <typename HT>
 __device__ __forceinline__ int tile_forest(const TileArgs<HT>& a, const TileQ<HT>& q,
-                                           const int* off, int tile, int lane) {
+                                           const int* off, int item, int lane) {
   using Q = TileQ<HT>;
   // the arguments used in the loops, held in registers (stores through other
   // pointers would otherwise force reloads)
@@ -145,9 +162,10 @@ __device__ __forceinline__ int tile_forest(const TileArgs<HT>& a, const TileQ<HT
   const uint8_t* const mask = a.mask;
   const uint8_t* const code = a.code;
   const HT* const h = a.h;
-  // level 0: the tile's cells without receiver, in row order
+  // level 0: the item's cells without receiver, in row order
   int n = 0;
   {
+    const int tile = item >> 2, part = item & 3;
     const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
     constexpr int TH = tile_h<HT>();
     const int x = tx * kTileW + lane, y0 = ty * TH;
@@ -155,7 +173,8 @@ __device__ __forceinline__ int tile_forest(const TileArgs<HT>& a, const TileQ<HT
 #pragma unroll
     for (int r = 0; r < TH; ++r) {
       const int y = y0 + r;
-      cd[r] = (x < nx && y < ny) ? code[(size_t)y * nx + x] : 0;
+      const bool row = part == 0 || (part == 1) == (r < TH / 2);
+      cd[r] = (x < nx && y < ny && row) ? code[(size_t)y * nx + x] : 0;
     }
 #pragma unroll
     for (int r = 0; r < TH; ++r) {
@@ -298,8 +317,9 @@ __device__ __noinline__ int block_tier(const StepArgs<HT, CT>& a, Shared& s, int
   uint8_t* pqk = a.pqk + (size_t)b * a.pcap;
   constexpr int TH = tile_h<HT>();
   for (int i = w; i < nov; i += kWarps) {
-    int cd[TH], x, y0;
-    tile_codes<TH>(a.code, s.ovf_tiles[i], a.tiles_x, nx, ny, lane, cd, &x, &y0);
+    int cd[TH], x, y0, tile, rlo, rhi;
+    item_rows<TH>(s.ovf_tiles[i], &tile, &rlo, &rhi);
+    tile_codes<TH>(a.code, tile, rlo, rhi, a.tiles_x, nx, ny, lane, cd, &x, &y0);
 #pragma unroll
     for (int r = 0; r < TH; ++r) {
       const bool f = cd[r] >= kSink;
@@ -337,7 +357,6 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   const TileQ<HT> q(dyn_smem + w * kWarpBytes);
-  const int T = a.ntiles;
   if (t == 0) {
     s.n_ovf = 0;
     s.n0 = 0;
@@ -362,17 +381,29 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
   ta.ero.dt = a.dt;
   ta.ero.Udt_f = a.Udt_f;
   long long mine = 0;
-  // tiles are claimed one at a time from a device-wide counter; the next
-  // claim is issued before the current tile is processed
-  int tile = 0;
-  if (lane == 0) tile = atomicAdd(tiles_next, 1);
-  tile = __shfl_sync(0xffffffffu, tile, 0);
-  while (tile < T) {
+  // work items are claimed one at a time from a device-wide counter, the
+  // next claim issued before the current item is processed.  Claims below
+  // T - S are whole tiles; the last S tiles (one per four warps of the
+  // grid) are claimed as halves, so the last claims are half as long.
+  // Lane 0 maps a claim to its item (-1: none left).
+  constexpr int TH = tile_h<HT>();
+  const auto item_of = [&](int claim) {
+    const int T = a.ntiles;
+    const int S = min(T, (int)gridDim.x * (kWarps / 4)), TF = T - S;
+    if (claim >= T + S) return -1;
+    return claim < TF ? tile_item(claim, 0)
+                      : tile_item(TF + ((claim - TF) >> 1), 1 + ((claim - TF) & 1));
+  };
+  int item = 0;
+  if (lane == 0) item = item_of(atomicAdd(tiles_next, 1));
+  item = __shfl_sync(0xffffffffu, item, 0);
+  while (item >= 0) {
     int next = 0;
     if (lane == 0) next = atomicAdd(tiles_next, 1);
-    const int r = tile_forest(ta, q, s.off, tile, lane);
-    const int cur = tile;
-    tile = __shfl_sync(0xffffffffu, next, 0);
+    const int r = tile_forest(ta, q, s.off, item, lane);
+    if (lane == 0) next = item_of(next);
+    const int cur = item;
+    item = __shfl_sync(0xffffffffu, next, 0);
     if (r >= 0) {
       mine += r;
       continue;
@@ -383,8 +414,7 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
     if (i < kOvfCap) {
       if (lane == 0) s.ovf_tiles[i] = cur;
     } else {
-      push_tile_roots_device<tile_h<HT>()>(a.code, a.queue, dev_roots, cur, a.tiles_x, a.nx,
-                                           a.ny, lane);
+      push_tile_roots_device<TH>(a.code, a.queue, dev_roots, cur, a.tiles_x, a.nx, a.ny, lane);
     }
   }
   // per-warp totals (lane 0's count is the warp's)
