@@ -12,6 +12,7 @@ flushed (a 512 MiB write) between timed steps, outside the events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   # the CPU oracle on the host cores
+  python bench.py --sweep                # edge 100 .. 16000, O(N^x) per region
 
 Under torchrun each rank advances its own replica of the grid (one grid does
 not shard: its level order is global); the reported value is the sum over
@@ -64,6 +65,10 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--sweep", action="store_true",
+                    help="time the FP64 step at edge lengths 100 .. 16000 and fit the\n"
+                         "wall-time exponent x of O(N^x) per edge-length region")
+    ap.add_argument("--sweep-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -604,10 +609,93 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
 
 
+# Edge-length regions of the paper's GPU scaling table (Table 2): upper edge
+# bounds and the wall-time exponents x of O(N^x) it reports in each.
+SWEEP_REGIONS = (("A", 400, 0.33), ("B", 1000, 0.16), ("C", 2500, 0.42), ("D", 16000, 0.92))
+SWEEP_EDGES = (100, 141, 200, 283, 400, 566, 800, 1000, 1414, 2000, 2500, 2828, 4000, 5657,
+               8000, 11314, 16000)
+
+
+def fit_exponents(edges, ms, regions=SWEEP_REGIONS):
+    """Least-squares slope of log(time) against log(cells) in each region;
+    a region spans the edges from the previous region's bound to its own,
+    both bounds included (a point on a bound belongs to both sides)."""
+    edges = np.asarray(edges, dtype=np.float64)
+    t = np.asarray(ms, dtype=np.float64)
+    out, lo = {}, 0.0
+    for name, hi, _ in regions:
+        sel = (edges >= lo) & (edges <= hi)
+        if sel.sum() >= 2:
+            x = np.log(edges[sel] ** 2)
+            y = np.log(t[sel])
+            out[name] = float(np.polyfit(x, y, 1)[0])
+        else:
+            out[name] = None
+        lo = hi
+    return out
+
+
+def run_sweep(args):
+    """The paper's scaling experiment (Table 2) on the tiered FP64 step: per
+    edge length, seeded [0,1) noise with the 256^2 workload's parameters,
+    warm-up steps, then single-step launches timed with CUDA events, L2
+    flushed between them; prints one JSON line."""
+    import torch
+    from paper_1803_02977_gb300 import lem, synth
+
+    dev = torch.device("cuda", 0)
+    w = synth.workload("grid256_f64")
+    flush = torch.empty(args.flush_mib << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(0)
+    clocks.start()
+    points = []
+    for e in SWEEP_EDGES:
+        h = torch.tensor(synth.noise_surface(e, e, w.seed), device=dev)
+        mdl = lem.Model(h, dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt)
+        for _ in range(max(3, args.warmup)):
+            mdl.step(1)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.sweep_steps)]
+        torch.cuda.synchronize()
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            mdl.step(1)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        mdl.sync()
+        tiers = lem.lem_tier_stats(mdl.ctx)
+        tl = traced_step(lem, mdl, flush)
+        mdl.close()
+        del h
+        ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+        n = e * e
+        ss = (tl or {}).get("steady_state_step") or {}
+        points.append({"edge": e, "cells": n, "ms_per_step": ms,
+                       "cell_steps_per_s": n / (ms / 1e3),
+                       "warp_tier_fraction": tiers[0] / max(1, sum(tiers)),
+                       "trace_first_step_us": round((tl or {}).get("total_us", 0.0), 1),
+                       "trace_steady_step_us": {k: round(v, 1)
+                                                for k, v in (ss.get("us") or {}).items()}})
+    clk = clocks.stop()
+    fit = fit_exponents([p["edge"] for p in points], [p["ms_per_step"] for p in points])
+    print(json.dumps({"sweep": "tiered step, FP64, int32 counts", "metric": "ms/step",
+                      "steps_timed": args.sweep_steps, "data": "synthetic",
+                      "l2": f"flushed between timed steps ({args.flush_mib} MiB write)",
+                      "points": points, "fit_x": fit,
+                      "paper_x": {n: x for n, _, x in SWEEP_REGIONS},
+                      "region_max_edge": {n: hi for n, hi, _ in SWEEP_REGIONS},
+                      "clocks": clk}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 

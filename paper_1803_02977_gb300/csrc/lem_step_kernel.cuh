@@ -180,10 +180,12 @@ __device__ __forceinline__ bool no_rounding_merge(typename Bits<HT>::U m, typena
 // high word is unique in the group; no other member can round to the same
 // slope when none has the next high word (then it lies more than 2^32 of the
 // minimum's ulps above it) and the minimum lies at most 18 binades below h_c
-// (so the 2^32 ulps between consecutive high words exceed 4 ulps of h_c).  The two candidates' slopes
-// are compared in FP32 from the high words (relative error below 2^-19
-// each), deciding when they differ by more than 2^-16 of h_c plus 2^-16 of
-// the slopes.  Returns -1 when any of this does not hold.
+// (so the 2^32 ulps between consecutive high words exceed 4 ulps of h_c).
+// The two candidates' slopes are compared in FP32 from the high words
+// (relative error below 2^-19 each), deciding when they differ by more than
+// 2^-16 of h_c plus 2^-16 of the slopes.  Returns -1 when any of this does
+// not hold (a minimum far below h_c, as the zero perimeter is for its
+// interior neighbours, included).
 __device__ __forceinline__ int receiver_code_hi_words(const unsigned hc, const unsigned* x) {
   unsigned worst = hc;
 #pragma unroll
@@ -224,14 +226,12 @@ __device__ __forceinline__ int receiver_code_hi(const double hcd, const double* 
   return receiver_code_hi_words((unsigned)__double2hiint(hcd), x);
 }
 
+// The group minima by bit patterns and the winners' slopes in FP64 (see
+// above), without the high-word first try.
 template <typename HT>
-__device__ __forceinline__ int receiver_code_vals(const HT hcv, const HT* v) {
+__device__ __forceinline__ int receiver_code_exact(const HT hcv, const HT* v) {
   using B = Bits<HT>;
   using U = typename B::U;
-  if constexpr (sizeof(HT) == 8) {
-    const int k = receiver_code_hi(hcv, v);
-    if (k >= 0) return k;
-  }
   const U bc = B::of(hcv);
   U mC = bc, mD = bc, rC = bc, rD = bc;  // group minima and runners-up below hc
   int kC = kSink, kD = kSink;
@@ -276,6 +276,15 @@ __device__ __forceinline__ int receiver_code_vals(const HT hcv, const HT* v) {
   return receiver_code_slow((double)hcv, (double)v[0], (double)v[1], (double)v[2],
                             (double)v[3], (double)v[4], (double)v[5], (double)v[6],
                             (double)v[7]);
+}
+
+template <typename HT>
+__device__ __forceinline__ int receiver_code_vals(const HT hcv, const HT* v) {
+  if constexpr (sizeof(HT) == 8) {
+    const int k = receiver_code_hi(hcv, v);
+    if (k >= 0) return k;
+  }
+  return receiver_code_exact(hcv, v);
 }
 
 // Alg 1 for FP32 elevations: the same result as receiver_code<float>, with

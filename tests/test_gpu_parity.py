@@ -37,6 +37,21 @@ def _tilted(nx, ny, seed, slope=0.05):
     return h
 
 
+def _far_minima(nx, ny, seed):
+    # neighbours far below a cell (zero, denormal, tiny) mixed with ones
+    # just inside and just beyond 18 binades below it, singly and in pairs:
+    # the receivers' high-word path takes one far group minimum as 0 and
+    # must leave two far members, or any doubt, to the exact comparison
+    h = 0.5 + synth.uniform01(seed, nx * ny).reshape(ny, nx)
+    r = synth.uniform01(seed + 1, nx * ny).reshape(ny, nx)
+    for lo, val in ((0.00, 0.0), (0.05, 5e-324), (0.08, 1e-300), (0.11, 2.0 ** -20),
+                    (0.14, 2.0 ** -19), (0.17, 2.0 ** -19 * (1 - 2.0 ** -40)),
+                    (0.20, 2.0 ** -18), (0.23, 2.0 ** -20 * (1 + 2.0 ** -21))):
+        h[(r >= lo) & (r < lo + 0.03)] = val
+    h[0, :] = h[-1, :] = h[:, 0] = h[:, -1] = 0.0
+    return h
+
+
 CASES = [
     ("3x3", lambda: synth.noise_surface(3, 3, 1)),
     ("5x4", lambda: synth.noise_surface(5, 4, 2)),
@@ -49,6 +64,7 @@ CASES = [
     ("tilted_300x200", lambda: _tilted(300, 200, 6)),
     ("tilted_1500x64", lambda: _tilted(1500, 64, 7, slope=0.2)),
     ("1031x777_int", lambda: _int_grid(1031, 777, 8, levels=40)),
+    ("far_minima_300x200", lambda: _far_minima(300, 200, 31)),
 ]
 
 
@@ -180,6 +196,7 @@ STEP_CASES = [
     # row pitch not a multiple of 16 bytes: strips staged element-wise, not by TMA
     ("noise_odd_257x190", lambda: synth.noise_surface(257, 190, 4), "tiles"),
     ("noise_tilt_700x500", lambda: synth.noise_surface(700, 500, 3, south_tilt=1e-4), "tiles"),
+    ("far_minima_300x200", lambda: _far_minima(300, 200, 31), None),
     ("int_300x300", lambda: _int_grid(300, 300, 9, levels=12), None),
     # one chain of ~300 cells per row, rooted on the west edge: too deep for a
     # warp's tile; the block or the device tier takes them, depending on how
