@@ -170,6 +170,8 @@ def erode(h, rec, queue_, levels, cnt, p):
 
 
 def erode_newton(h, rec, queue_, levels, cnt, p, n_exp, eps=1e-12, max_iter=100):
+    """Alg 6 for general n-hat (Newton-Raphson from h0) in place on a (ny, nx)
+    float64 array already uplifted."""
     ny, nx = h.shape
     levels = np.ascontiguousarray(levels, dtype=np.int64)
     lib().orc_erode_newton(nx, ny, _p(h), _p(np.ascontiguousarray(rec, np.int32)),
@@ -201,6 +203,16 @@ def step(h, p, frozen_rec=None):
     hn = np.array(h, dtype=np.float64, copy=True)
     uplift(hn, p)
     erode(hn, g.rec, g.queue, g.levels, g.cnt, p)
+    return hn, g
+
+
+def step_newton(h, p, n_exp, eps=1e-12, max_iter=100, frozen_rec=None):
+    """One full step with Alg 6's Newton iteration for a general n-hat;
+    returns (h_next, StepGraph)."""
+    g = StepGraph(h, frozen_rec)
+    hn = np.array(h, dtype=np.float64, copy=True)
+    uplift(hn, p)
+    erode_newton(hn, g.rec, g.queue, g.levels, g.cnt, p, n_exp, eps, max_iter)
     return hn, g
 
 

@@ -202,6 +202,10 @@ void orc_erode_newton(int nx, int ny, double* h, const int32_t* rec, const int32
       double F = p->K * p->dt * pow(A, p->m) / pow(orc_dist(nx, c, r, p->dx), n_exp);
       double h0 = h[c];
       double hn = h[r];
+      /* (h - h_r)^n-hat is undefined below the receiver for non-integer
+       * n-hat: a cell whose uplifted elevation is not above its receiver's
+       * new elevation keeps it (no erosion without a downhill slope). */
+      if (!(h0 - hn > 0.0)) continue;
       double hnew = h0;      /* current updated value */
       double hp = h0;        /* previous updated value */
       double delta = 2.0 * eps;

@@ -93,10 +93,16 @@ void orc_erode(int nx, int ny, double* h, const int32_t* rec, const int32_t* que
                const int64_t* levels, int64_t nlevels, const int64_t* cnt, const orc_params* p);
 
 /* Alg 6 for general n-hat: the Newton-Raphson iteration of Alg 6 from
- * h_new = h0 until |delta| <= eps or max_iter iterations.  For n-hat = 1 it
- * reaches the closed form after one step (up to rounding).
- * Pinned: n-hat = 1 agreement with orc_erode; residual of the implicit
- * equation below eps at every cell. */
+ * h_new = h0 until |delta| <= eps or max_iter iterations, with
+ * F = K dt A^m / dist^n-hat.  For n-hat = 1 it reaches the closed form after
+ * one step (up to rounding).  Reading: a cell whose uplifted elevation h0 is
+ * not above its receiver's new elevation keeps h0 (the power of a
+ * non-positive slope is undefined for non-integer n-hat; with a uniform
+ * uplift this never happens, since the sweep preserves strict descent).
+ * Pinned: n-hat = 1 agreement with orc_erode; n-hat = 2 against the root of
+ * the quadratic at every cell; one iteration against one Newton update
+ * written out; the 1-D channel steady state (slope/d)^n = U/(K A^m) for
+ * n-hat = 1.5 and 3; residual of the implicit equation at every cell. */
 void orc_erode_newton(int nx, int ny, double* h, const int32_t* rec, const int32_t* queue,
                       const int64_t* levels, int64_t nlevels, const int64_t* cnt,
                       const orc_params* p, double n_exp, double eps, int max_iter);
