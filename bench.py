@@ -358,6 +358,17 @@ def run_ours(args):
             v32 = N / (float(np.mean(ms32)) / 1e3)
             forms["fp32_same_grid"] = {"workload": "grid2048_f32", "ms_per_step": float(np.mean(ms32)),
                                        "value": v32, "vs_plain_fp64": v32 / plain}
+            # Alg 6 with n-hat = 2 (Newton sweep on device-wide levels), next to
+            # the n-hat = 1 step on the same device-wide levels (mode 1)
+            msn = time_grid(lem, w, min(K, 20), 3, flush, dev, slope_exponent=2.0)
+            msd = time_grid(lem, w, min(K, 20), 3, flush, dev, mode=1)
+            vn = N / (float(np.mean(msn)) / 1e3)
+            vd = N / (float(np.mean(msd)) / 1e3)
+            forms["slope_exponent_n2"] = {"workload": w.name, "n_hat": 2.0, "eps_m": 1e-12,
+                                          "max_iter": 100, "ms_per_step": float(np.mean(msn)),
+                                          "value": vn, "vs_plain_fp64": vn / plain,
+                                          "device_wide_n1": {"ms_per_step": float(np.mean(msd)),
+                                                             "value": vd}}
         w10 = synth.workload("grid10000_f32")
         ms10 = time_grid(lem, w10, 5, 2, flush, dev)
         a10 = sum(algo_bytes(4, 8).values()) * w10.cells / (float(np.mean(ms10)) / 1e3) / 1e9
@@ -421,14 +432,20 @@ def run_ours(args):
     return 0
 
 
-def time_grid(lem, w, steps, warmup, flush, dev):
-    """Per-step device times (ms) of `steps` single-step launches on workload
-    w, L2 flushed between steps; returns (step_ms, final levels)."""
+def time_grid(lem, w, steps, warmup, flush, dev, slope_exponent=None, mode=None):
+    """Per-step device times (ms) of `steps` single-step lem_step calls on
+    workload w, L2 flushed between steps.  slope_exponent: Alg 6's Newton
+    form with that n-hat (eps 1e-12 m, at most 100 updates); mode: the
+    lem_set_step_mode form."""
     import torch
     P = 8 if w.dtype == "f64" else 4
     count_bits = 64 if w.area_dtype == "i64" else 32
     h = torch.tensor(w.initial().astype(np.float64 if P == 8 else np.float32), device=dev)
     mdl = lem.Model(h, dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt, count_bits=count_bits)
+    if slope_exponent is not None:
+        mdl.set_slope_exponent(slope_exponent, 1e-12, 100)
+    if mode is not None:
+        lem.lem_set_step_mode(mdl.ctx, mode)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         mdl.step(1)

@@ -5,8 +5,9 @@
  * Landscape Evolution Model with Parallelism" (arXiv:1803.02977), Section
  * "The Algorithm": receivers (Alg 1), donors (Alg 2), the breadth-first
  * queue of levels (Alg 3), flow accumulation (Alg 4, Eq. 2), uplift (Alg 5)
- * and implicit stream-power erosion for n-hat = 1 (Alg 6, Eq. 1), repeated
- * ("Rinse, Repeat").
+ * and implicit stream-power erosion (Alg 6, Eq. 1: the closed form for
+ * n-hat = 1, Newton-Raphson for other exponents), repeated ("Rinse,
+ * Repeat").
  *
  * Conventions shared by every entry point
  *  - Grid: width nx, height ny, cell (x, y) at address c = y*nx + x, rows
@@ -150,8 +151,36 @@ LEM_API int lem_erode(lem_ctx* ctx);
 
 /* "Rinse, Repeat": nsteps full time steps (receivers through erosion) in
  * one cooperative persistent launch with device-wide barriers between
- * levels; no host round trip between levels or steps. */
+ * levels; no host round trip between levels or steps.  With a slope
+ * exponent other than 1 (lem_set_slope_exponent) each step is two
+ * cooperative launches: Algs 1-4 on device-wide levels, then the Newton
+ * sweep of Alg 6. */
 LEM_API int lem_step(lem_ctx* ctx, int nsteps);
+
+/* Alg 6 (Step 7) for a general slope exponent n-hat (Eq. 1, erosion rate
+ * K A^m S^n-hat).  Later lem_erode and lem_step calls solve each eroding
+ * cell's implicit update
+ *     h - h0 + F (h - h_r)^n = 0,   F = K*dt*(count*area_scale)^m / d^n,
+ * h0 = h + dt*U, d = dx or dx*sqrt(2), h_r the receiver's new elevation, by
+ * Alg 6's Newton-Raphson iteration from h = h0, in FP64 for either elevation
+ * type (FP32 results are rounded once).  The iteration stops once an update
+ * changes h by at most eps metres, or after max_iter updates (Alg 6's text
+ * allows a fixed count in place of the tolerance test).  A cell whose h0 is
+ * not above h_r keeps h0: the power of a non-positive slope is undefined for
+ * non-integer n.
+ *  n         slope exponent, finite and >= 1.  Then f(h) is convex and
+ *            increasing above h_r, so the iterates fall monotonically to the
+ *            root and stay above h_r; for n < 1 the first update can cross
+ *            below h_r, so n < 1 is rejected.  n = 1 restores the closed
+ *            form of lem_erode (the default); eps and max_iter are then
+ *            ignored.
+ *  eps       tolerance in metres, finite and > 0
+ *  max_iter  1 .. 1000
+ * Returns LEM_EINVAL for other values.  While n != 1, lem_step runs Algs 3-6
+ * on device-wide levels for every step (lem_set_step_mode's private tiers
+ * evaluate only n = 1) and lem_adjoint returns LEM_EINVAL.  Takes effect at
+ * the next launch; no device work. */
+LEM_API int lem_set_slope_exponent(lem_ctx* ctx, double n, double eps, int max_iter);
 
 /* Freeze the receiver graph: dev_rec (nx*ny int32, self = NoFlow, every
  * other entry an in-grid neighbour, perimeter cells self) replaces Alg 1 in

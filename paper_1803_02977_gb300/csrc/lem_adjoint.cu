@@ -381,6 +381,7 @@ extern "C" LEM_API int lem_adjoint(lem_ctx* c, const double* dev_h0, const doubl
   if (!c || !dev_h0 || !dev_lambda_T || !dev_dLdU || !dLdK || nsteps < 1 || ckpt_every < 1)
     return LEM_EINVAL;
   if (c->p.dtype != LEM_F64 || c->p.count_bits != 32) return LEM_EINVAL;
+  if (c->newton_iters > 0) return LEM_EINVAL;  // the sweep below is the n-hat = 1 adjoint
   const size_t N = (size_t)c->N;
   const int nck = (nsteps + ckpt_every - 1) / ckpt_every;
   const int seglen = ckpt_every < nsteps ? ckpt_every : nsteps;

@@ -18,6 +18,9 @@
 
 using namespace lem;
 
+template <typename HT, typename CT>
+int lem_newton_launch(const StepArgs<HT, CT>& a, int grid, cudaStream_t stream);
+
 
 
 namespace {
@@ -183,6 +186,11 @@ StepArgs<HT, CT> make_args(lem_ctx* c, int phases, int nsteps) {
   a.phases = phases;
   a.nsteps = nsteps;
   a.frozen = c->frozen ? 1 : 0;
+  a.newton_iters = c->newton_iters;
+  a.nexp = c->nexp;
+  a.neps = c->neps;
+  a.dxn = c->dxn;
+  a.dxdn = c->dxdn;
   return a;
 }
 
@@ -193,6 +201,20 @@ int launch_typed(lem_ctx* c, int phases, int nsteps) {
   LEM_CUDA(cudaLaunchCooperativeKernel(step_kernel_ptr<HT, CT>(), dim3(c->grid), dim3(kBD), args,
                                        kDynSmem, c->stream));
   return LEM_OK;
+}
+
+// Alg 6 for a general slope exponent: its own cooperative kernel
+// (lem_newton.cu) over the device-wide levels of the last levels phase.
+template <typename HT, typename CT>
+int launch_newton_typed(lem_ctx* c) {
+  const StepArgs<HT, CT> a = make_args<HT, CT>(c, kPhEro, 1);
+  return lem_newton_launch<HT, CT>(a, c->grid, c->stream);
+}
+
+int launch_newton(lem_ctx* c) {
+  const bool f64 = c->p.dtype == LEM_F64, c64 = c->p.count_bits == 64;
+  if (f64) return c64 ? launch_newton_typed<double, long long>(c) : launch_newton_typed<double, int>(c);
+  return c64 ? launch_newton_typed<float, long long>(c) : launch_newton_typed<float, int>(c);
 }
 
 int launch_step(lem_ctx* c, int phases, int nsteps) {
@@ -513,7 +535,7 @@ int lem_erode(lem_ctx* c) {
   if (!c) return LEM_EINVAL;
   if (!c->h) return LEM_ESTATE;
   if (!c->acc_valid) return LEM_ESTATE;
-  int rc = launch_step(c, kPhEro, 1);
+  int rc = c->newton_iters > 0 ? launch_newton(c) : launch_step(c, kPhEro, 1);
   if (rc != LEM_OK) return rc;
   if (!c->frozen) c->rec_valid = c->lev_valid = c->acc_valid = false;
   return LEM_OK;
@@ -523,12 +545,41 @@ int lem_step(lem_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return LEM_EINVAL;
   if (!c->h) return LEM_ESTATE;
   if (nsteps == 0) return LEM_OK;
+  if (c->newton_iters > 0) {
+    // general slope exponent: Algs 1-4 on device-wide levels, then the
+    // Newton sweep, two launches per step
+    for (int s = 0; s < nsteps; ++s) {
+      int rc = launch_step(c, kPhRec | kPhLev | kPhAcc, 1);
+      if (rc != LEM_OK) return rc;
+      rc = launch_newton(c);
+      if (rc != LEM_OK) return rc;
+    }
+    c->rec_valid = c->lev_valid = c->acc_valid = c->frozen;
+    return LEM_OK;
+  }
   int rc = launch_step(c, c->mode == 0 ? kPhTiles : kPhAll, nsteps);
   if (rc != LEM_OK) return rc;
   // A frozen graph's codes and masks stay current; the device-wide queue and
   // counts are current only if the device-wide form ran (mode 1).
   c->rec_valid = c->frozen;
   c->lev_valid = c->acc_valid = c->frozen && c->mode == 1;
+  return LEM_OK;
+}
+
+int lem_set_slope_exponent(lem_ctx* c, double n, double eps, int max_iter) {
+  if (!c || !is_finite(n) || n < 1.0) return LEM_EINVAL;
+  if (n == 1.0) {
+    c->newton_iters = 0;
+    c->nexp = 1.0;
+    c->neps = c->dxn = c->dxdn = 0.0;
+    return LEM_OK;
+  }
+  if (!is_finite(eps) || !(eps > 0.0) || max_iter < 1 || max_iter > 1000) return LEM_EINVAL;
+  c->newton_iters = max_iter;
+  c->nexp = n;
+  c->neps = eps;
+  c->dxn = std::pow(c->p.dx, n);
+  c->dxdn = std::pow(c->dxd, n);
   return LEM_OK;
 }
 

@@ -36,6 +36,10 @@ struct lem_ctx {
   int* host_status = nullptr;  // pinned: [err, nlevels]
   bool rec_valid = false, lev_valid = false, acc_valid = false, frozen = false;
   double Kdt = 0, dxd = 0, area_scale = 0;
+  // Alg 6 for a general slope exponent (lem_set_slope_exponent); 0 updates =
+  // the n = 1 closed form
+  int newton_iters = 0;
+  double nexp = 1.0, neps = 0.0, dxn = 0.0, dxdn = 0.0;
   double wait_limit_s = 2.0;
   unsigned long long* trace = nullptr;  // device trace buffer (lem_trace_enable)
   lem::TmaDesc tmap{};      // TMA descriptor of the bound h (host copy)

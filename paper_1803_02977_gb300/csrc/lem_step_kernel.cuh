@@ -77,6 +77,10 @@ struct StepArgs {
   int phases;
   int nsteps;
   int frozen;           // receivers frozen: codes are inputs, not recomputed
+  // Alg 6 for a general slope exponent (erode_newton): updates per cell, 0 for
+  // the n = 1 closed form; exponent, tolerance, dx^n and (dx*sqrt2)^n
+  int newton_iters = 0;
+  double nexp = 1.0, neps = 0.0, dxn = 0.0, dxdn = 0.0;
 };
 
 constexpr int kCodeGuard = 16;     // 0xFF guard bytes on each side of the code array
@@ -517,9 +521,40 @@ __device__ __forceinline__ HT erode_value(const StepArgs<HT, CT>& a, int c, int 
   }
 }
 
+// Alg 6 for a general slope exponent n (Eq. 1 with S^n): Newton-Raphson on
+// f(h) = h - h0 + F*(h - hr)^n from h = h0 = h + dt*U, F = K*dt*A^m / d^n,
+// stopped once an update moves h by at most eps or after newton_iters
+// updates.  FP64 for either elevation type.  For n >= 1, f is convex and
+// increasing above hr, so the iterates fall monotonically to the root and
+// stay above hr.  A cell whose h0 is not above hr keeps h0: the power of a
+// non-positive slope is undefined for non-integer n.  Kept out of line so
+// that the n = 1 loops around it are compiled as before.
+template <typename HT, typename CT>
+__device__ __noinline__ HT erode_newton(const StepArgs<HT, CT>& a, int c, int k, CT count,
+                                        HT hcur, HT hrecv) {
+  const double hr = (double)hrecv;
+  const double h0 = (double)hcur + uplift_dt(a, c);
+  if (!(h0 - hr > 0.0)) return (HT)h0;
+  const double A = (double)count * a.area_scale;
+  const double F = a.Kdt * pow(A, a.m) / (nbr_diag(k) ? a.dxdn : a.dxn);
+  const double n = a.nexp;
+  double hn = h0, hp = h0;
+  for (int it = 0; it < a.newton_iters; ++it) {
+    const double x = hn - hr;
+    const double p = (n == 2.0) ? x : pow(x, n - 1.0);  // x^(n-1)
+    const double f = (hn - h0) + F * (p * x);
+    const double fp = 1.0 + F * n * p;
+    hn = hn - f / fp;
+    const double d = hn - hp;
+    hp = hn;
+    if (!(fabs(d) > a.neps)) break;
+  }
+  return (HT)hn;
+}
+
 // Erode up to kItems cells (entries < 0 are skipped) with all loads issued
 // before the arithmetic.
-template <typename HT, typename CT>
+template <bool kNewton, typename HT, typename CT>
 __device__ __forceinline__ void erode_items(const StepArgs<HT, CT>& a, const int* cs) {
   int ks[kItems];
   CT ns[kItems];
@@ -535,9 +570,14 @@ __device__ __forceinline__ void erode_items(const StepArgs<HT, CT>& a, const int
 #pragma unroll
   for (int i = 0; i < kItems; ++i)
     if (cs[i] >= 0) hr[i] = a.h[cs[i] + nbr_off(ks[i], a.nx)];
+  if constexpr (kNewton) {
+    for (int i = 0; i < kItems; ++i)
+      if (cs[i] >= 0) a.h[cs[i]] = erode_newton(a, cs[i], ks[i], ns[i], hc[i], hr[i]);
+  } else {
 #pragma unroll
-  for (int i = 0; i < kItems; ++i)
-    if (cs[i] >= 0) a.h[cs[i]] = erode_value(a, cs[i], ks[i], ns[i], hc[i], hr[i]);
+    for (int i = 0; i < kItems; ++i)
+      if (cs[i] >= 0) a.h[cs[i]] = erode_value(a, cs[i], ks[i], ns[i], hc[i], hr[i]);
+  }
 }
 
 // ---- Alg 4 ------------------------------------------------------------------------
@@ -1222,7 +1262,9 @@ __device__ __noinline__ bool phase_global_accumulate(const StepArgs<HT, CT>& a, 
 }
 
 // ---- phase: device-wide Algs 5-6 ---------------------------------------------------
-template <typename HT, typename CT>
+// kNewton: Alg 6's Newton iteration for a general slope exponent
+// (erode_newton) in place of the n = 1 closed form.
+template <typename HT, typename CT, bool kNewton = false>
 __device__ __noinline__ bool phase_global_erode(const StepArgs<HT, CT>& a, int L) {
   const unsigned G = gridDim.x;
   const int b = blockIdx.x, t = threadIdx.x;
@@ -1242,7 +1284,7 @@ __device__ __noinline__ bool phase_global_erode(const StepArgs<HT, CT>& a, int L
           if (hi - lo > kNarrow) break;
           for (int j = lo + t; j < hi; j += kBD) {
             int cs[kItems] = {a.queue[j], -1, -1, -1};
-            erode_items(a, cs);
+            erode_items<kNewton>(a, cs);
           }
           __syncthreads();
           ++ll;
@@ -1262,7 +1304,7 @@ __device__ __noinline__ bool phase_global_erode(const StepArgs<HT, CT>& a, int L
         const int j = base + i * gstride;
         cs[i] = (j < hi) ? a.queue[j] : -1;
       }
-      erode_items(a, cs);
+      erode_items<kNewton>(a, cs);
     }
     if (!grid_barrier(a.st, G)) return false;
     trace_point(a.st, kTrEroWide + l);

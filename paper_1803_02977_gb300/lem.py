@@ -49,6 +49,7 @@ SIGNATURES = [
     ("lem_accumulate", _I, [_VP, _VP]),
     ("lem_erode", _I, [_VP]),
     ("lem_step", _I, [_VP, _I]),
+    ("lem_set_slope_exponent", _I, [_VP, _D, _D, _I]),
     ("lem_set_receivers", _I, [_VP, _VP]),
     ("lem_sync", _I, [_VP]),
     ("lem_set_wait_limit", _I, [_VP, _D]),
@@ -169,6 +170,10 @@ def lem_erode(ctx):
 
 def lem_step(ctx, nsteps):
     _check(lib().lem_step(ctx, nsteps), "lem_step")
+
+
+def lem_set_slope_exponent(ctx, n, eps=1e-12, max_iter=100):
+    _check(lib().lem_set_slope_exponent(ctx, n, eps, max_iter), "lem_set_slope_exponent")
 
 
 def lem_set_receivers(ctx, rec):
@@ -409,6 +414,9 @@ class Model:
 
     def set_receivers(self, rec):
         lem_set_receivers(self.ctx, rec)
+
+    def set_slope_exponent(self, n, eps=1e-12, max_iter=100):
+        lem_set_slope_exponent(self.ctx, n, eps, max_iter)
 
     def sync(self):
         lem_sync(self.ctx)
