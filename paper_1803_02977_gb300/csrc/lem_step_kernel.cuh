@@ -853,36 +853,51 @@ __device__ __forceinline__ void codes_strip_f64(const double* S, uint8_t* code, 
   auto hw = [&](int r, int col) -> unsigned {
     return reinterpret_cast<const unsigned*>(S + r * kStageCols + col)[1];
   };
+  // the exact comparison for a cell the high words leave undecided, its
+  // nine doubles reloaded from the staged strip (r: staged row below it)
+  auto exact = [&](int r) -> int {
+    const double* up = S + (r - 2) * kStageCols + sc;
+    const double* md = up + kStageCols;
+    const double* dn = md + kStageCols;
+    const double v[8] = {up[-1], up[0], up[1], md[-1], md[1], dn[-1], dn[0], dn[1]};
+    return receiver_code_vals(md[0], v);
+  };
   unsigned ul = hw(0, sc - 1), uc = hw(0, sc), ur = hw(0, sc + 1);
   unsigned ml = hw(1, sc - 1), mc = hw(1, sc), mr = hw(1, sc + 1);
   long long at = (long long)(y0 - 1) * nx + x;
   unsigned pw = 0;
-  for (int y = y0 - 1; y <= y1; ++y, at += nx) {
-    const int r = y + 1 - yb;  // staged row below the cell
+  // two rows per iteration (y and y + 1): their receiver decisions are
+  // independent, so the scheduler can interleave them
+  for (int y = y0 - 1; y <= y1; y += 2, at += 2 * (long long)nx) {
+    const bool two = y + 1 <= y1;  // the same for the whole warp
+    const int r = y + 1 - yb;      // staged row below row y
+    const int r2 = two ? r + 1 : r;
     const unsigned dl = hw(r, sc - 1), dc = hw(r, sc), dr = hw(r, sc + 1);
-    int cd = 0xFF;
-    if (xin && y >= 0 && y < ny) {
-      if (xperim || y == 0 || y == ny - 1) {
-        cd = kEdge;
-      } else {
-        const unsigned xs[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
-        cd = receiver_code_hi_words(mc, xs);
-        if (cd < 0) {
-          const double* up = S + (r - 2) * kStageCols + sc;
-          const double* md = up + kStageCols;
-          const double* dn = md + kStageCols;
-          const double v[8] = {up[-1], up[0], up[1], md[-1], md[1], dn[-1], dn[0], dn[1]};
-          cd = receiver_code_vals(md[0], v);
-        }
-      }
-      if (own && y >= y0 && y < y1) code[at] = (uint8_t)cd;
-    }
-    ul = ml; uc = mc; ur = mr;
-    ml = dl; mc = dc; mr = dr;
-    pw = ((pw >> 8) & 0xFFFFu) | (pointer_bits(cd) << 16);
-    const unsigned pl = __shfl_up_sync(0xffffffffu, pw, 1);
-    const unsigned pr = __shfl_down_sync(0xffffffffu, pw, 1);
+    const unsigned el = hw(r2, sc - 1), ec = hw(r2, sc), er = hw(r2, sc + 1);
+    const unsigned xs0[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
+    const unsigned xs1[8] = {ml, mc, mr, dl, dr, el, ec, er};
+    int c0 = receiver_code_hi_words(mc, xs0);
+    int c1 = receiver_code_hi_words(dc, xs1);
+    const bool in0 = xin && y >= 0 && y < ny;
+    const bool in1 = two && xin && y + 1 < ny;  // y + 1 >= 0 always
+    c0 = !in0 ? 0xFF : ((xperim || y == 0 || y == ny - 1) ? kEdge : c0);
+    c1 = !in1 ? 0xFF : ((xperim || y + 1 == 0 || y + 1 == ny - 1) ? kEdge : c1);
+    if (c0 < 0) c0 = exact(r);
+    if (c1 < 0) c1 = exact(r2);
+    if (own && in0 && y >= y0 && y < y1) code[at] = (uint8_t)c0;
+    if (own && in1 && y + 1 < y1) code[at + nx] = (uint8_t)c1;
+    pw = ((pw >> 8) & 0xFFFFu) | (pointer_bits(c0) << 16);
+    unsigned pl = __shfl_up_sync(0xffffffffu, pw, 1);
+    unsigned pr = __shfl_down_sync(0xffffffffu, pw, 1);
     if (own && y > y0 && y <= y1) mask[at - nx] = (uint8_t)mask_from_pointers(pl, pw, pr);
+    if (two) {
+      pw = ((pw >> 8) & 0xFFFFu) | (pointer_bits(c1) << 16);
+      pl = __shfl_up_sync(0xffffffffu, pw, 1);
+      pr = __shfl_down_sync(0xffffffffu, pw, 1);
+      if (own && y + 1 > y0) mask[at] = (uint8_t)mask_from_pointers(pl, pw, pr);
+    }
+    ul = dl; uc = dc; ur = dr;
+    ml = el; mc = ec; mr = er;
   }
 }
 
