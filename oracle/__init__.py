@@ -71,6 +71,10 @@ def lib():
         L.orc_uplift.argtypes = [i32, i32, vp, pp]
         L.orc_erode.argtypes = [i32, i32, vp, vp, vp, vp, i64, vp, pp]
         L.orc_erode_newton.argtypes = [i32, i32, vp, vp, vp, vp, i64, vp, pp, dbl, dbl, i32]
+        L.orc_fill_eps.argtypes = [i32, i32, vp, vp]
+        L.orc_fill_eps.restype = i32
+        L.orc_fill_eps_f32.argtypes = [i32, i32, vp, vp]
+        L.orc_fill_eps_f32.restype = i32
         L.orc_run.argtypes = [i32, i32, vp, i32, pp, vp, vp]
         L.orc_run.restype = i32
         L.orc_adjoint_step.argtypes = [i32, i32, vp, vp, vp, vp, i64, vp, pp, vp, vp, vp,
@@ -204,6 +208,23 @@ def step(h, p, frozen_rec=None):
     uplift(hn, p)
     erode(hn, g.rec, g.queue, g.levels, g.cnt, p)
     return hn, g
+
+
+def fill(h):
+    """Depression filling with epsilon increments (Priority-Flood) of a
+    (ny, nx) float64 or float32 array; returns the filled array (same dtype)."""
+    ny, nx = h.shape
+    if h.dtype == np.float32:
+        src = np.ascontiguousarray(h, np.float32)
+        out = np.empty_like(src)
+        rc = lib().orc_fill_eps_f32(nx, ny, _p(src), _p(out))
+    else:
+        src = np.ascontiguousarray(h, np.float64)
+        out = np.empty_like(src)
+        rc = lib().orc_fill_eps(nx, ny, _p(src), _p(out))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return out
 
 
 def step_newton(h, p, n_exp, eps=1e-12, max_iter=100, frozen_rec=None):

@@ -223,6 +223,117 @@ void orc_erode_newton(int nx, int ny, double* h, const int32_t* rec, const int32
   }
 }
 
+/* ---- Depression filling before receivers (Section "Local Minima") -------- */
+/* Priority-Flood with epsilon increments: cells leave one priority queue in
+ * order of their filled elevation w (ties by address), starting from the
+ * perimeter at w = h; each neighbour n seen for the first time gets
+ * w[n] = max(h[n], next representable value above w[c]) and joins the
+ * queue.  One queue for every cell keeps the pops in non-decreasing w, so a
+ * cell's first w is its least one. */
+
+typedef struct {
+  double w;
+  int64_t c;
+} orc_pq_item;
+
+static int orc_pq_less(const orc_pq_item* a, const orc_pq_item* b) {
+  return a->w < b->w || (a->w == b->w && a->c < b->c);
+}
+
+static void orc_pq_push(orc_pq_item* q, int64_t* n, orc_pq_item it) {
+  int64_t i = (*n)++;
+  q[i] = it;
+  while (i > 0) {
+    int64_t parent = (i - 1) / 2;
+    if (!orc_pq_less(&q[i], &q[parent])) break;
+    orc_pq_item t = q[i];
+    q[i] = q[parent];
+    q[parent] = t;
+    i = parent;
+  }
+}
+
+static orc_pq_item orc_pq_pop(orc_pq_item* q, int64_t* n) {
+  orc_pq_item top = q[0];
+  q[0] = q[--(*n)];
+  int64_t i = 0;
+  for (;;) {
+    int64_t l = 2 * i + 1, r = l + 1, m = i;
+    if (l < *n && orc_pq_less(&q[l], &q[m])) m = l;
+    if (r < *n && orc_pq_less(&q[r], &q[m])) m = r;
+    if (m == i) break;
+    orc_pq_item t = q[i];
+    q[i] = q[m];
+    q[m] = t;
+    i = m;
+  }
+  return top;
+}
+
+/* The flood on values held as doubles; `f32` rounds every filled value to
+ * float and steps by float ulps (the FP32 form). */
+static int orc_fill_impl(int nx, int ny, const double* h, double* w, int f32) {
+  int64_t n = (int64_t)nx * ny;
+  uint8_t* closed = (uint8_t*)calloc((size_t)n, 1);
+  orc_pq_item* q = (orc_pq_item*)malloc(sizeof(orc_pq_item) * (size_t)(n > 0 ? n : 1));
+  if (!closed || !q) {
+    free(closed);
+    free(q);
+    return -1;
+  }
+  int64_t qn = 0;
+  for (int y = 0; y < ny; ++y) {
+    for (int x = 0; x < nx; ++x) {
+      if (!orc_on_perimeter(nx, ny, x, y)) continue;
+      int64_t c = (int64_t)y * nx + x;
+      w[c] = h[c];
+      closed[c] = 1;
+      orc_pq_item it = {w[c], c};
+      orc_pq_push(q, &qn, it);
+    }
+  }
+  while (qn > 0) {
+    orc_pq_item it = orc_pq_pop(q, &qn);
+    int64_t c = it.c;
+    int x = (int)(c % nx), y = (int)(c / nx);
+    double up = f32 ? (double)nextafterf((float)w[c], INFINITY) : nextafter(w[c], INFINITY);
+    for (int k = 0; k < 8; ++k) {
+      int xn = x + ORC_DX[k], yn = y + ORC_DY[k];
+      if (xn < 0 || yn < 0 || xn >= nx || yn >= ny) continue;
+      int64_t nb = (int64_t)yn * nx + xn;
+      if (closed[nb]) continue;
+      closed[nb] = 1;
+      w[nb] = h[nb] > up ? h[nb] : up;
+      orc_pq_item nt = {w[nb], nb};
+      orc_pq_push(q, &qn, nt);
+    }
+  }
+  free(closed);
+  free(q);
+  return 0;
+}
+
+int orc_fill_eps(int nx, int ny, const double* h, double* w) {
+  return orc_fill_impl(nx, ny, h, w, 0);
+}
+
+int orc_fill_eps_f32(int nx, int ny, const float* h, float* w) {
+  int64_t n = (int64_t)nx * ny;
+  double* hd = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* wd = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!hd || !wd) {
+    free(hd);
+    free(wd);
+    return -1;
+  }
+  for (int64_t c = 0; c < n; ++c) hd[c] = (double)h[c];
+  int rc = orc_fill_impl(nx, ny, hd, wd, 1);
+  for (int64_t c = 0; c < n && rc == 0; ++c) w[c] = (float)wd[c];
+  free(hd);
+  free(wd);
+  return rc;
+}
+
 /* ---- Rinse, Repeat -------------------------------------------------------- */
 
 int orc_run(int nx, int ny, double* h, int nsteps, const orc_params* p,

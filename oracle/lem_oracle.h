@@ -107,6 +107,23 @@ void orc_erode_newton(int nx, int ny, double* h, const int32_t* rec, const int32
                       const int64_t* levels, int64_t nlevels, const int64_t* cnt,
                       const orc_params* p, double n_exp, double eps, int max_iter);
 
+/* Depression filling before Alg 1 (Section "Local Minima": fill depressions
+ * to their outlets by Priority-Flood, resolving the resulting flats as part
+ * of the flood).  w receives the least surface with w >= h, w = h on the
+ * perimeter, and every interior cell strictly above its lowest neighbour:
+ *     w[c] = max(h[c], next double above min over the 8 neighbours of w),
+ * so Alg 1 on w finds a receiver for every interior cell.  Elevations must
+ * be finite.  Priority-Flood with one priority queue (ties by address).
+ * Returns 0, or -1 on allocation failure.
+ * Pinned: the fixed-point equation at every cell; Bellman-Ford relaxation
+ * on tiny grids; hand-computed nested basins; no interior sink remains;
+ * a surface already draining to the perimeter is unchanged. */
+int orc_fill_eps(int nx, int ny, const double* h, double* w);
+
+/* The same for FP32 elevations: w and its increments in float (next float
+ * above). */
+int orc_fill_eps_f32(int nx, int ny, const float* h, float* w);
+
 /* "Rinse, Repeat": nsteps full time steps in place on h.  If frozen_rec is
  * non-NULL it replaces Alg 1 in every step.  If nlevels_out is non-NULL it
  * receives L for each step.  Returns 0, or -1 on allocation failure. */
