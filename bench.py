@@ -364,6 +364,7 @@ def run_ours(args):
             msd = time_grid(lem, w, min(K, 20), 3, flush, dev, mode=1)
             vn = N / (float(np.mean(msn)) / 1e3)
             vd = N / (float(np.mean(msd)) / 1e3)
+            forms["fill"] = measure_fill(lem, w, flush, dev, plain)
             forms["slope_exponent_n2"] = {"workload": w.name, "n_hat": 2.0, "eps_m": 1e-12,
                                           "max_iter": 100, "ms_per_step": float(np.mean(msn)),
                                           "value": vn, "vs_plain_fp64": vn / plain,
@@ -432,11 +433,11 @@ def run_ours(args):
     return 0
 
 
-def time_grid(lem, w, steps, warmup, flush, dev, slope_exponent=None, mode=None):
+def time_grid(lem, w, steps, warmup, flush, dev, slope_exponent=None, mode=None, fill=False):
     """Per-step device times (ms) of `steps` single-step lem_step calls on
     workload w, L2 flushed between steps.  slope_exponent: Alg 6's Newton
     form with that n-hat (eps 1e-12 m, at most 100 updates); mode: the
-    lem_set_step_mode form."""
+    lem_set_step_mode form; fill: depression filling before every step."""
     import torch
     P = 8 if w.dtype == "f64" else 4
     count_bits = 64 if w.area_dtype == "i64" else 32
@@ -446,6 +447,8 @@ def time_grid(lem, w, steps, warmup, flush, dev, slope_exponent=None, mode=None)
         mdl.set_slope_exponent(slope_exponent, 1e-12, 100)
     if mode is not None:
         lem.lem_set_step_mode(mdl.ctx, mode)
+    if fill:
+        mdl.set_fill(True)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         mdl.step(1)
@@ -463,6 +466,44 @@ def time_grid(lem, w, steps, warmup, flush, dev, slope_exponent=None, mode=None)
     ms = [a.elapsed_time(b) for a, b in ev]
     mdl.close()
     return ms
+
+
+def measure_fill(lem, w, flush, dev, plain, reps=5):
+    """Depression filling (lem_fill) of workload w's initial surface: device
+    time per flood (a fresh copy of the surface each time, L2 flushed), the
+    rounds it took, and the time step with filling before every step."""
+    import torch
+    h0 = torch.tensor(w.initial(), device=dev)
+    h = h0.clone()
+    mdl = lem.Model(h, dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt)
+    stream = torch.cuda.current_stream()
+    ms = []
+    for r in range(reps + 2):
+        h.copy_(h0)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mdl.fill()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r >= 2:
+            ms.append(e0.elapsed_time(e1))
+    mdl.sync()
+    rounds, visits, passes, unsettled = lem.lem_fill_stats(mdl.ctx)
+    changed = int((h != h0).sum().item())
+    mdl.close()
+    mss = time_grid(lem, w, 10, 3, flush, dev, fill=True)
+    N = w.cells
+    f_ms = float(np.median(ms))
+    # algorithmic bytes of a flood: read h, write the filled h
+    gbs = 2 * (8 if w.dtype == "f64" else 4) * N / (f_ms / 1e3) / 1e9
+    return {"workload": w.name, "ms_per_fill": f_ms, "rounds": rounds,
+            "tile_visits": visits, "passes": passes, "unsettled_visits": unsettled,
+            "cells_changed": changed, "cells_per_s": N / (f_ms / 1e3),
+            "algo_gbs_read_h_write_h": gbs,
+            "step_with_fill": {"ms_per_step": float(np.mean(mss)),
+                               "value": N / (float(np.mean(mss)) / 1e3),
+                               "vs_plain_fp64": N / (float(np.mean(mss)) / 1e3) / plain}}
 
 
 def measure_batch(lem, steps, ws, rank, dev, count=512, sample_every=8):

@@ -182,6 +182,33 @@ LEM_API int lem_step(lem_ctx* ctx, int nsteps);
  * the next launch; no device work. */
 LEM_API int lem_set_slope_exponent(lem_ctx* ctx, double n, double eps, int max_iter);
 
+/* Depression filling before Alg 1 (Section "Local Minima": depressions
+ * filled to the level of their outlets by Priority-Flood, the flats this
+ * leaves resolved as part of the flood).  Replaces the bound elevations, in
+ * place, by the least surface w with w >= h, w = h on the perimeter and every
+ * interior cell strictly above its lowest neighbour:
+ *     w[c] = max(h[c], next representable value above min over the eight
+ *            neighbours of w),
+ * so that Alg 1 then finds a receiver for every interior cell and all flow
+ * reaches the perimeter.  Increments are one unit in the last place of the
+ * elevation type (double or float).  The result is unique and bit-exact;
+ * elevations must be finite.  One cooperative launch, asynchronous on the
+ * context's stream; the first call allocates a scratch of nx*ny elevations
+ * plus two bytes per 32 x 32 tile.  LEM_ETIMEOUT (reported by the next
+ * synchronising call) if a device wait ran out.  Invalidates the derived
+ * stages. */
+LEM_API int lem_fill(lem_ctx* ctx);
+
+/* With on = 1, every later lem_step step begins with lem_fill (each step is
+ * then its own launches); on = 0 (the default) turns it off. */
+LEM_API int lem_set_fill(lem_ctx* ctx, int on);
+
+/* Work of the last lem_fill (zeros if none ran; synchronises the stream):
+ * stats[0] rounds (grid barriers between tile sweeps), stats[1] tile visits,
+ * stats[2] relaxation passes over all visits, stats[3] visits that ran out
+ * of passes and were revisited in the next round.  stats holds 4 entries. */
+LEM_API int lem_fill_stats(lem_ctx* ctx, int64_t* stats);
+
 /* Freeze the receiver graph: dev_rec (nx*ny int32, self = NoFlow, every
  * other entry an in-grid neighbour, perimeter cells self) replaces Alg 1 in
  * every later stage and step until called again with NULL.  The graph is

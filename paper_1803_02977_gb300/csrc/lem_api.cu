@@ -20,6 +20,7 @@ using namespace lem;
 
 template <typename HT, typename CT>
 int lem_newton_launch(const StepArgs<HT, CT>& a, int grid, cudaStream_t stream);
+int lem_fill_launch(lem_ctx* c);
 
 
 
@@ -437,6 +438,9 @@ void lem_destroy(lem_ctx* c) {
   cudaFree(c->pqf);
   cudaFree(c->cntq);
   cudaFree(c->trace);
+  cudaFree(c->fill_w);
+  cudaFree(c->fill_dirty);
+  cudaFree(c->fill_state);
   if (c->host_status) cudaFreeHost(c->host_status);
   delete c;
 }
@@ -545,16 +549,26 @@ int lem_step(lem_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return LEM_EINVAL;
   if (!c->h) return LEM_ESTATE;
   if (nsteps == 0) return LEM_OK;
-  if (c->newton_iters > 0) {
-    // general slope exponent: Algs 1-4 on device-wide levels, then the
-    // Newton sweep, two launches per step
+  if (c->newton_iters > 0 || c->fill_on) {
+    // one step at a time: the depression flood first (lem_set_fill), then
+    // either the step kernel or, for a general slope exponent, Algs 1-4 on
+    // device-wide levels and the Newton sweep
     for (int s = 0; s < nsteps; ++s) {
-      int rc = launch_step(c, kPhRec | kPhLev | kPhAcc, 1);
-      if (rc != LEM_OK) return rc;
-      rc = launch_newton(c);
+      int rc = LEM_OK;
+      if (c->fill_on) {
+        rc = lem_fill_launch(c);
+        if (rc != LEM_OK) return rc;
+      }
+      if (c->newton_iters > 0) {
+        rc = launch_step(c, kPhRec | kPhLev | kPhAcc, 1);
+        if (rc == LEM_OK) rc = launch_newton(c);
+      } else {
+        rc = launch_step(c, c->mode == 0 ? kPhTiles : kPhAll, 1);
+      }
       if (rc != LEM_OK) return rc;
     }
-    c->rec_valid = c->lev_valid = c->acc_valid = c->frozen;
+    c->rec_valid = c->frozen;
+    c->lev_valid = c->acc_valid = c->frozen && (c->newton_iters > 0 || c->mode == 1);
     return LEM_OK;
   }
   int rc = launch_step(c, c->mode == 0 ? kPhTiles : kPhAll, nsteps);

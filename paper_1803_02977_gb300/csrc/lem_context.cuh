@@ -40,6 +40,12 @@ struct lem_ctx {
   // the n = 1 closed form
   int newton_iters = 0;
   double nexp = 1.0, neps = 0.0, dxn = 0.0, dxdn = 0.0;
+  // depression filling (lem_fill.cu): scratch allocated by the first flood
+  int fill_on = 0;             // lem_step floods before every step
+  int fill_grid = 0;           // co-resident blocks of the flood kernel
+  void* fill_w = nullptr;      // relaxed surface, nx*ny elements
+  uint8_t* fill_dirty = nullptr;  // two per-tile flag arrays
+  void* fill_state = nullptr;  // round counters
   double wait_limit_s = 2.0;
   unsigned long long* trace = nullptr;  // device trace buffer (lem_trace_enable)
   lem::TmaDesc tmap{};      // TMA descriptor of the bound h (host copy)

@@ -50,6 +50,9 @@ SIGNATURES = [
     ("lem_erode", _I, [_VP]),
     ("lem_step", _I, [_VP, _I]),
     ("lem_set_slope_exponent", _I, [_VP, _D, _D, _I]),
+    ("lem_fill", _I, [_VP]),
+    ("lem_set_fill", _I, [_VP, _I]),
+    ("lem_fill_stats", _I, [_VP, _I64P]),
     ("lem_set_receivers", _I, [_VP, _VP]),
     ("lem_sync", _I, [_VP]),
     ("lem_set_wait_limit", _I, [_VP, _D]),
@@ -174,6 +177,21 @@ def lem_step(ctx, nsteps):
 
 def lem_set_slope_exponent(ctx, n, eps=1e-12, max_iter=100):
     _check(lib().lem_set_slope_exponent(ctx, n, eps, max_iter), "lem_set_slope_exponent")
+
+
+def lem_fill(ctx):
+    _check(lib().lem_fill(ctx), "lem_fill")
+
+
+def lem_set_fill(ctx, on):
+    _check(lib().lem_set_fill(ctx, 1 if on else 0), "lem_set_fill")
+
+
+def lem_fill_stats(ctx):
+    """(rounds, tile visits, relaxation passes, unsettled visits) of the last flood."""
+    v = (ctypes.c_int64 * 4)()
+    _check(lib().lem_fill_stats(ctx, v), "lem_fill_stats")
+    return tuple(int(x) for x in v)
 
 
 def lem_set_receivers(ctx, rec):
@@ -417,6 +435,12 @@ class Model:
 
     def set_slope_exponent(self, n, eps=1e-12, max_iter=100):
         lem_set_slope_exponent(self.ctx, n, eps, max_iter)
+
+    def fill(self):
+        lem_fill(self.ctx)
+
+    def set_fill(self, on):
+        lem_set_fill(self.ctx, on)
 
     def sync(self):
         lem_sync(self.ctx)
