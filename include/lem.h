@@ -194,7 +194,7 @@ LEM_API int lem_set_slope_exponent(lem_ctx* ctx, double n, double eps, int max_i
  * elevation type (double or float).  The result is unique and bit-exact;
  * elevations must be finite.  One cooperative launch, asynchronous on the
  * context's stream; the first call allocates a scratch of nx*ny elevations
- * plus two bytes per 32 x 32 tile.  LEM_ETIMEOUT (reported by the next
+ * and nx*ny int32 plus two bytes per 32 x 32 tile.  LEM_ETIMEOUT (reported by the next
  * synchronising call) if a device wait ran out.  Invalidates the derived
  * stages. */
 LEM_API int lem_fill(lem_ctx* ctx);

@@ -441,6 +441,7 @@ void lem_destroy(lem_ctx* c) {
   cudaFree(c->fill_w);
   cudaFree(c->fill_dirty);
   cudaFree(c->fill_state);
+  cudaFree(c->fill_ptr);
   if (c->host_status) cudaFreeHost(c->host_status);
   delete c;
 }

@@ -45,6 +45,7 @@ struct lem_ctx {
   int fill_grid = 0;           // co-resident blocks of the flood kernel
   void* fill_w = nullptr;      // relaxed surface, nx*ny elements
   uint8_t* fill_dirty = nullptr;  // two per-tile flag arrays
+  int* fill_ptr = nullptr;     // chain pointers, nx*ny
   void* fill_state = nullptr;  // round counters
   double wait_limit_s = 2.0;
   unsigned long long* trace = nullptr;  // device trace buffer (lem_trace_enable)

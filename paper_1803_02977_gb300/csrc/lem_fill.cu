@@ -18,6 +18,14 @@
 // Rounds end at a bounded grid barrier; the flood is done after a round in
 // which no tile changed.
 //
+// The start need not be +inf everywhere: any w0 >= T(w0) (T the right-hand
+// side above) decreases onto the same fixed point.  w0 = h is such a start at
+// every cell whose chain of lowest strictly lower neighbours ends on the
+// perimeter (each cell of the chain has a neighbour below it that keeps its
+// h), so the kernel first finds every chain's end by pointer jumping and
+// starts from +inf only in the basins of interior pits and flats.  Only the
+// tiles holding such cells are relaxed in the first round.
+//
 // The relaxation runs on order-preserving integer keys of the elevations
 // (FillKey): min and max become integer operations and the next value up is
 // key + 1, which equals IEEE nextafter(x, +inf) for every finite x (-0 is
@@ -81,6 +89,7 @@ template <> struct FillKey<float> {
 struct FillState {
   int claim[3];  // tiles claimed in the round
   int mark[3];   // some tile was marked dirty for the next round
+  int jump[3];   // some pointer moved in the pointer-jumping pass
   int rounds;    // rounds the last flood took
   int visits;    // tile visits (dirty tiles relaxed) in the last flood
   unsigned long long passes;  // relaxation passes over all visits
@@ -92,7 +101,8 @@ struct FillArgs {
   int nx, ny, tiles_x, ntiles, max_rounds;
   HT* h;           // in: the surface; out: the filled surface
   typename FillKey<HT>::K* w;  // scratch: keys of the relaxed surface, nx*ny
-  uint8_t* dirty;  // two arrays of ntiles flags, by round parity
+  int* ptr;        // scratch: lowest lower neighbour, then the chain's end
+  uint8_t* dirty;  // two arrays of ntiles flags, by round parity (zero on entry)
   FillState* fs;
   DevState* st;
 };
@@ -192,12 +202,60 @@ __global__ void __launch_bounds__(fill_warps<HT>() * 32, 1)
   const int nx = a.nx, ny = a.ny;
   const long long N = (long long)nx * ny;
   const unsigned G = gridDim.x;
-  // w = h on the perimeter, +inf inside
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N;
-       c += (long long)G * blockDim.x) {
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gstride = (long long)G * blockDim.x;
+  // each cell's lowest strictly lower neighbour (lowest k among equals), or
+  // itself: perimeter cells, and interior pits and flats
+  for (long long c = gtid; c < N; c += gstride) {
     const int y = (int)(c / nx), x = (int)(c - (long long)y * nx);
-    const bool perim = x == 0 || y == 0 || x == nx - 1 || y == ny - 1;
-    a.w[c] = perim ? FK::of(a.h[c]) : FK::kInf;
+    int to = (int)c;
+    if (x > 0 && y > 0 && x < nx - 1 && y < ny - 1) {
+      K best = FK::of(a.h[c]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int n = (int)c + nbr_off(k, nx);
+        const K kn = FK::of(a.h[n]);
+        if (kn < best) {
+          best = kn;
+          to = n;
+        }
+      }
+    }
+    a.ptr[c] = to;
+  }
+  if (!grid_barrier(a.st, G)) return;
+  // pointer jumping until every pointer names its chain's end (chains are
+  // strictly descending, so they end; in-place jumps only shorten them)
+  for (int j = 0;; ++j) {
+    bool moved = false;
+    for (long long c = gtid; c < N; c += gstride) {
+      const int p = __ldcg(a.ptr + c);
+      const int pp = __ldcg(a.ptr + p);
+      if (pp != p) {
+        __stcg(a.ptr + c, pp);
+        moved = true;
+      }
+    }
+    if (__syncthreads_or(moved) && threadIdx.x == 0) a.fs->jump[j % 3] = 1;
+    if (!grid_barrier(a.st, G)) return;
+    if (lead) a.fs->jump[(j + 2) % 3] = 0;
+    if (ld_volatile(&a.fs->jump[j % 3]) == 0) break;
+    if (j >= 64) {  // a chain of 2^64 cells: cannot happen
+      set_error(a.st, kErrInval);
+      return;
+    }
+  }
+  // w = h where the chain ends on the perimeter, +inf in the basins of
+  // interior pits and flats; their tiles are dirty for the first round
+  for (long long c = gtid; c < N; c += gstride) {
+    const int e = __ldcg(a.ptr + c);
+    const int ey = e / nx, ex = e - ey * nx;
+    const bool drains = ex == 0 || ey == 0 || ex == nx - 1 || ey == ny - 1;
+    a.w[c] = drains ? FK::of(a.h[c]) : FK::kInf;
+    if (!drains) {
+      const int y = (int)(c / nx), x = (int)(c - (long long)y * nx);
+      a.dirty[(y / kFT) * a.tiles_x + x / kFT] = 1;
+    }
   }
   if (!grid_barrier(a.st, G)) return;
   int r = 0;
@@ -271,21 +329,23 @@ int fill_launch_typed(lem_ctx* c) {
     if (e == cudaSuccess) c->fill_grid = nsm * per_sm;
     if (e == cudaSuccess) e = cudaMalloc(&c->fill_w, (size_t)c->N * sizeof(HT));
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->fill_dirty, 2 * (size_t)ntiles);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->fill_ptr, (size_t)c->N * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->fill_state, sizeof(FillState));
     if (e != cudaSuccess) {
       cudaFree(c->fill_w);
       cudaFree(c->fill_dirty);
       cudaFree(c->fill_state);
+      cudaFree(c->fill_ptr);
+      c->fill_ptr = nullptr;
       c->fill_w = nullptr;
       c->fill_dirty = nullptr;
       c->fill_state = nullptr;
       return e == cudaErrorMemoryAllocation ? LEM_ENOMEM : LEM_ECUDA;
     }
   }
-  // round 0 visits every tile; counters start at zero
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->fill_dirty, 1, (size_t)ntiles, c->stream);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(c->fill_dirty + ntiles, 0, (size_t)ntiles, c->stream);
+  // no tile is dirty until the kernel marks the basins' tiles; counters
+  // start at zero
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->fill_dirty, 0, 2 * (size_t)ntiles, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->fill_state, 0, sizeof(FillState), c->stream);
   FillArgs<HT> a;
   a.nx = c->p.nx;
@@ -299,6 +359,7 @@ int fill_launch_typed(lem_ctx* c) {
   a.h = (HT*)c->h;
   a.w = (typename FillKey<HT>::K*)c->fill_w;
   a.dirty = c->fill_dirty;
+  a.ptr = c->fill_ptr;
   a.fs = (FillState*)c->fill_state;
   a.st = c->st;
   void* args[] = {&a};

@@ -88,7 +88,7 @@ def test_fill_bit_exact(name, make, dtype):
     assert got.dtype == want.dtype
     assert np.array_equal(got, want), f"{name}: {np.count_nonzero(got != want)} cells differ"
     rounds, visits, passes, _ = lem.lem_fill_stats(mdl.ctx)
-    assert rounds >= 1 and visits >= 1 and passes >= visits
+    assert rounds >= 1 and passes >= visits >= 0
     # filling a filled surface changes nothing
     mdl.fill()
     mdl.sync()
