@@ -470,8 +470,9 @@ def time_grid(lem, w, steps, warmup, flush, dev, slope_exponent=None, mode=None,
 
 def measure_fill(lem, w, flush, dev, plain, reps=5):
     """Depression filling (lem_fill) of workload w's initial surface: device
-    time per flood (a fresh copy of the surface each time, L2 flushed), the
-    rounds it took, and the time step with filling before every step."""
+    time per flood (a fresh copy of the surface each time, L2 flushed) and
+    the work it took; then, on the evolving surface, a flood followed by a
+    time step, the two timed separately."""
     import torch
     h0 = torch.tensor(w.initial(), device=dev)
     h = h0.clone()
@@ -492,18 +493,47 @@ def measure_fill(lem, w, flush, dev, plain, reps=5):
     rounds, visits, passes, unsettled = lem.lem_fill_stats(mdl.ctx)
     changed = int((h != h0).sum().item())
     mdl.close()
-    mss = time_grid(lem, w, 10, 3, flush, dev, fill=True)
+    # the evolving surface: a flood, then a step, three times untimed, then
+    # both timed separately (with L, the level count of the filled surface)
+    h.copy_(h0)
+    mdl = lem.Model(h, dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt)
+    fms, sms = [], []
+    for r in range(3 + 4):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        flush.zero_()
+        evs[0].record(stream)
+        mdl.fill()
+        evs[1].record(stream)
+        mdl.step(1)
+        evs[2].record(stream)
+        torch.cuda.synchronize()
+        if r >= 3:
+            fms.append(evs[0].elapsed_time(evs[1]))
+            sms.append(evs[1].elapsed_time(evs[2]))
+    mdl.sync()
+    tiers = lem.lem_tier_stats(mdl.ctx)
+    ev_rounds = lem.lem_fill_stats(mdl.ctx)[0]
+    mdl.fill()
+    mdl.receivers()
+    L = lem.lem_levels(mdl.ctx)
+    mdl.close()
     N = w.cells
     f_ms = float(np.median(ms))
     # algorithmic bytes of a flood: read h, write the filled h
     gbs = 2 * (8 if w.dtype == "f64" else 4) * N / (f_ms / 1e3) / 1e9
+    step_ms = float(np.mean(fms)) + float(np.mean(sms))
     return {"workload": w.name, "ms_per_fill": f_ms, "rounds": rounds,
             "tile_visits": visits, "passes": passes, "unsettled_visits": unsettled,
             "cells_changed": changed, "cells_per_s": N / (f_ms / 1e3),
             "algo_gbs_read_h_write_h": gbs,
-            "step_with_fill": {"ms_per_step": float(np.mean(mss)),
-                               "value": N / (float(np.mean(mss)) / 1e3),
-                               "vs_plain_fp64": N / (float(np.mean(mss)) / 1e3) / plain}}
+            "evolving_surface": {
+                "ms_per_fill": float(np.mean(fms)), "fill_rounds": ev_rounds,
+                "ms_per_step_after_fill": float(np.mean(sms)),
+                "levels_of_filled_surface": L,
+                "tier_cells": {"warp_tiles": tiers[0], "block_queues": tiers[1],
+                               "device_wide": tiers[2]},
+                "ms_per_fill_and_step": step_ms, "value": N / (step_ms / 1e3),
+                "vs_plain_fp64": N / (step_ms / 1e3) / plain}}
 
 
 def measure_batch(lem, steps, ws, rank, dev, count=512, sample_every=8):
