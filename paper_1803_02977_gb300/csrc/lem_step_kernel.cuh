@@ -81,13 +81,18 @@ struct StepArgs {
   // the n = 1 closed form; exponent, tolerance, dx^n and (dx*sqrt2)^n
   int newton_iters = 0;
   double nexp = 1.0, neps = 0.0, dxn = 0.0, dxdn = 0.0;
+  double dfac = 0.0, dfacd = 0.0;  // dx^(1-n) and (dx*sqrt2)^(1-n)
 };
 
 constexpr int kCodeGuard = 16;     // 0xFF guard bytes on each side of the code array
 constexpr int kBD = 1024;          // threads per block: one block per SM
 constexpr int kWarps = kBD / 32;
-constexpr int kNarrow = kBD;       // a device-wide level this small runs in block 0
 constexpr int kItems = 4;          // items per thread per round in wide loops
+// a device-wide level this small runs in block 0 alone, with block barriers
+// instead of grid barriers (up to two rounds of the breadth-first emission,
+// four cells per thread in the accumulation and erosion)
+constexpr int kNarrowBfs = 2 * kBD;
+constexpr int kNarrowSweep = kItems * kBD;
 constexpr int kPItems = 8;         // entries per thread per round of a private level
 constexpr int kStage = 16384;      // emitted entries staged in shared memory per round
 constexpr int kMaxPrivLevels = 2048;  // level offsets a private queue may hold
@@ -535,8 +540,15 @@ __device__ __noinline__ HT erode_newton(const StepArgs<HT, CT>& a, int c, int k,
   const double hr = (double)hrecv;
   const double h0 = (double)hcur + uplift_dt(a, c);
   if (!(h0 - hr > 0.0)) return (HT)h0;
-  const double A = (double)count * a.area_scale;
-  const double F = a.Kdt * pow(A, a.m) / (nbr_diag(k) ? a.dxdn : a.dxn);
+  // F = K*dt*A^m / d^n: for tabulated counts the n = 1 factor times d^(1-n)
+  const bool diag = nbr_diag(k);
+  double F;
+  if (count < (CT)kTableN) {
+    F = a.Ftab[(diag ? kTableN : 0) + (int)count].x * (diag ? a.dfacd : a.dfac);
+  } else {
+    const double A = (double)count * a.area_scale;
+    F = a.Kdt * pow(A, a.m) / (diag ? a.dxdn : a.dxn);
+  }
   const double n = a.nexp;
   double hn = h0, hp = h0;
   for (int it = 0; it < a.newton_iters; ++it) {
@@ -1127,7 +1139,7 @@ __device__ __noinline__ int phase_global_levels(const StepArgs<HT, CT>& a, Share
   int lo = 0, hi = hi0, l = 0;
   while (true) {
     const int S = hi - lo;
-    if (S <= kNarrow) {
+    if (S <= kNarrowBfs) {
       if (b == 0) {
         // block 0 alone: consecutive narrow levels, block barriers only
         bool done = false;
@@ -1154,7 +1166,7 @@ __device__ __noinline__ int phase_global_levels(const StepArgs<HT, CT>& a, Share
           lo = hi;
           hi = run;
           ++l;
-          if (hi - lo > kNarrow) break;
+          if (hi - lo > kNarrowBfs) break;
         }
         if (t == 0) {
           a.st->bfs_lo = lo;
@@ -1238,13 +1250,13 @@ __device__ __noinline__ bool phase_global_accumulate(const StepArgs<HT, CT>& a, 
   int l = L - 1;
   while (l >= 0) {
     int lo = a.levels[l], hi = a.levels[l + 1];
-    if (hi - lo <= kNarrow) {
+    if (hi - lo <= kNarrowSweep) {
       int ll = l;
       if (b == 0) {
         while (ll >= 0) {
           lo = a.levels[ll];
           hi = a.levels[ll + 1];
-          if (hi - lo > kNarrow) break;
+          if (hi - lo > kNarrowSweep) break;
           for (int j = lo + t; j < hi; j += kBD) {
             const int c = a.queue[j];
             a.cnt[c] = donor_sum(a.cnt, c, a.mask[c], a.nx);
@@ -1253,7 +1265,7 @@ __device__ __noinline__ bool phase_global_accumulate(const StepArgs<HT, CT>& a, 
           --ll;
         }
       } else {
-        while (ll >= 0 && a.levels[ll + 1] - a.levels[ll] <= kNarrow) --ll;
+        while (ll >= 0 && a.levels[ll + 1] - a.levels[ll] <= kNarrowSweep) --ll;
       }
       if (!grid_barrier(a.st, G)) return false;
       trace_point(a.st, kTrAccNarrow + ll + 1);
@@ -1290,13 +1302,13 @@ __device__ __noinline__ bool phase_global_erode(const StepArgs<HT, CT>& a, int L
   int l = 1;
   while (l < L) {
     int lo = a.levels[l], hi = a.levels[l + 1];
-    if (hi - lo <= kNarrow) {
+    if (hi - lo <= kNarrowSweep) {
       int ll = l;
       if (b == 0) {
         while (ll < L) {
           lo = a.levels[ll];
           hi = a.levels[ll + 1];
-          if (hi - lo > kNarrow) break;
+          if (hi - lo > kNarrowSweep) break;
           for (int j = lo + t; j < hi; j += kBD) {
             int cs[kItems] = {a.queue[j], -1, -1, -1};
             erode_items<kNewton>(a, cs);
@@ -1305,7 +1317,7 @@ __device__ __noinline__ bool phase_global_erode(const StepArgs<HT, CT>& a, int L
           ++ll;
         }
       } else {
-        while (ll < L && a.levels[ll + 1] - a.levels[ll] <= kNarrow) ++ll;
+        while (ll < L && a.levels[ll + 1] - a.levels[ll] <= kNarrowSweep) ++ll;
       }
       if (!grid_barrier(a.st, G)) return false;
       trace_point(a.st, kTrEroNarrow + ll);
