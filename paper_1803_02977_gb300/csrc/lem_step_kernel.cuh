@@ -497,33 +497,55 @@ __device__ __forceinline__ void uplift_sink(const StepArgs<HT, CT>& a, int c) {
 // instead of a division, which GB300 runs about seven times slower than an
 // FMA in FP64.  The results differ from the closed form by a few units in the
 // last place.  FP32 elevations use the same form with g rounded once to float.
+// g = F/(1+F) for a count beyond the tables, the same operations as the
+// tables (FP64 division; for FP32 contexts rounded to float by the caller).
 template <typename HT, typename CT>
-__device__ __forceinline__ HT erode_value(const StepArgs<HT, CT>& a, int c, int k, CT count,
-                                          HT hcur, HT hr) {
+__device__ __forceinline__ double big_count_g(const StepArgs<HT, CT>& a, CT count, bool diag) {
+  if constexpr (sizeof(HT) == 8) {
+    const double A = __dmul_rn((double)count, a.area_scale);
+    const double F = __ddiv_rn(__dmul_rn(a.Kdt, pow(A, a.m)), diag ? a.dxd : a.dx);
+    return __ddiv_rn(F, __dadd_rn(1.0, F));
+  } else {
+    const double A = (double)count * a.area_scale;
+    const double F = a.Kdt * pow(A, a.m) / (diag ? a.dxd : a.dx);
+    return F / (1.0 + F);
+  }
+}
+
+// The erosion factor g = F/(1+F) of a cell (double for FP64 elevations,
+// float for FP32).  gbig: when not null, big_count_g of every cell whose
+// count is beyond the tables, computed ahead of the level sweep
+// (phase_global_erode).
+template <typename HT, typename CT>
+__device__ __forceinline__ HT erode_factor(const StepArgs<HT, CT>& a, int c, int k, CT count,
+                                           const double* gbig) {
   const bool diag = nbr_diag(k);
   if constexpr (sizeof(HT) == 8) {
+    if (count < (CT)kTableN) return a.Ftab[(diag ? kTableN : 0) + (int)count].y;
+    return gbig ? gbig[c] : big_count_g(a, count, diag);
+  } else {
+    if (count < (CT)kTableN) return a.gtab[(diag ? kTableN : 0) + (int)count];
+    return (float)(gbig ? gbig[c] : big_count_g(a, count, diag));
+  }
+}
+
+// The increment form with a given factor g.
+template <typename HT, typename CT>
+__device__ __forceinline__ HT erode_apply(const StepArgs<HT, CT>& a, int c, HT g, HT hcur,
+                                          HT hr) {
+  if constexpr (sizeof(HT) == 8) {
     const double h0 = __dadd_rn(hcur, uplift_dt(a, c));
-    double g;
-    if (count < (CT)kTableN) {
-      g = a.Ftab[(diag ? kTableN : 0) + (int)count].y;
-    } else {
-      const double A = __dmul_rn((double)count, a.area_scale);
-      const double F = __ddiv_rn(__dmul_rn(a.Kdt, pow(A, a.m)), diag ? a.dxd : a.dx);
-      g = __ddiv_rn(F, __dadd_rn(1.0, F));
-    }
     return __fma_rn(-g, __dsub_rn(h0, hr), h0);
   } else {
-    float g;
-    if (count < (CT)kTableN) {
-      g = a.gtab[(diag ? kTableN : 0) + (int)count];
-    } else {
-      const double A = (double)count * a.area_scale;
-      const double F = a.Kdt * pow(A, a.m) / (diag ? a.dxd : a.dx);
-      g = (float)(F / (1.0 + F));
-    }
     const float h0 = __fadd_rn(hcur, uplift_dt_f(a, c));
     return __fmaf_rn(-g, __fsub_rn(h0, hr), h0);
   }
+}
+
+template <typename HT, typename CT>
+__device__ __forceinline__ HT erode_value(const StepArgs<HT, CT>& a, int c, int k, CT count,
+                                          HT hcur, HT hr) {
+  return erode_apply(a, c, erode_factor(a, c, k, count, (const double*)nullptr), hcur, hr);
 }
 
 // Alg 6 for a general slope exponent n (Eq. 1 with S^n): Newton-Raphson on
@@ -567,7 +589,8 @@ __device__ __noinline__ HT erode_newton(const StepArgs<HT, CT>& a, int c, int k,
 // Erode up to kItems cells (entries < 0 are skipped) with all loads issued
 // before the arithmetic.
 template <bool kNewton, typename HT, typename CT>
-__device__ __forceinline__ void erode_items(const StepArgs<HT, CT>& a, const int* cs) {
+__device__ __forceinline__ void erode_items(const StepArgs<HT, CT>& a, const int* cs,
+                                            const double* gbig) {
   int ks[kItems];
   CT ns[kItems];
   HT hc[kItems], hr[kItems];
@@ -588,7 +611,9 @@ __device__ __forceinline__ void erode_items(const StepArgs<HT, CT>& a, const int
   } else {
 #pragma unroll
     for (int i = 0; i < kItems; ++i)
-      if (cs[i] >= 0) a.h[cs[i]] = erode_value(a, cs[i], ks[i], ns[i], hc[i], hr[i]);
+      if (cs[i] >= 0)
+        a.h[cs[i]] = erode_apply(a, cs[i], erode_factor(a, cs[i], ks[i], ns[i], gbig), hc[i],
+                                 hr[i]);
   }
 }
 
@@ -1297,6 +1322,19 @@ __device__ __noinline__ bool phase_global_erode(const StepArgs<HT, CT>& a, int L
   const int b = blockIdx.x, t = threadIdx.x;
   const int gtid = b * kBD + t, gstride = (int)G * kBD;
   for (int j = gtid; j < a.levels[1]; j += gstride) uplift_sink(a, a.queue[j]);
+  // the factors of counts beyond the tables, ahead of the sweep, so that no
+  // level waits on their powers and divisions: stored by cell in the block
+  // tier's queue storage (at least nx*ny doubles, idle by now)
+  // (only for sweeps deep enough to pay for the pass over every count)
+  double* gbig = nullptr;
+  if (!kNewton && L > 64) {
+    gbig = reinterpret_cast<double*>(a.pq);
+    for (int j = a.levels[1] + gtid; j < a.levels[L]; j += gstride) {
+      const int c = a.queue[j];
+      const CT n = a.cnt[c];
+      if (n >= (CT)kTableN) gbig[c] = big_count_g(a, n, nbr_diag(a.code[c]));
+    }
+  }
   if (!grid_barrier(a.st, G)) return false;
   trace_point(a.st, kTrUplift);
   int l = 1;
@@ -1311,7 +1349,7 @@ __device__ __noinline__ bool phase_global_erode(const StepArgs<HT, CT>& a, int L
           if (hi - lo > kNarrowSweep) break;
           for (int j = lo + t; j < hi; j += kBD) {
             int cs[kItems] = {a.queue[j], -1, -1, -1};
-            erode_items<kNewton>(a, cs);
+            erode_items<kNewton>(a, cs, gbig);
           }
           __syncthreads();
           ++ll;
@@ -1331,7 +1369,7 @@ __device__ __noinline__ bool phase_global_erode(const StepArgs<HT, CT>& a, int L
         const int j = base + i * gstride;
         cs[i] = (j < hi) ? a.queue[j] : -1;
       }
-      erode_items<kNewton>(a, cs);
+      erode_items<kNewton>(a, cs, gbig);
     }
     if (!grid_barrier(a.st, G)) return false;
     trace_point(a.st, kTrEroWide + l);
