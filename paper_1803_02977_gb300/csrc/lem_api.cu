@@ -192,6 +192,8 @@ StepArgs<HT, CT> make_args(lem_ctx* c, int phases, int nsteps) {
   a.neps = c->neps;
   a.dxn = c->dxn;
   a.dxdn = c->dxdn;
+  a.dfac = c->dfac;
+  a.dfacd = c->dfacd;
   return a;
 }
 
@@ -586,7 +588,7 @@ int lem_set_slope_exponent(lem_ctx* c, double n, double eps, int max_iter) {
   if (n == 1.0) {
     c->newton_iters = 0;
     c->nexp = 1.0;
-    c->neps = c->dxn = c->dxdn = 0.0;
+    c->neps = c->dxn = c->dxdn = c->dfac = c->dfacd = 0.0;
     return LEM_OK;
   }
   if (!is_finite(eps) || !(eps > 0.0) || max_iter < 1 || max_iter > 1000) return LEM_EINVAL;
@@ -595,6 +597,8 @@ int lem_set_slope_exponent(lem_ctx* c, double n, double eps, int max_iter) {
   c->neps = eps;
   c->dxn = std::pow(c->p.dx, n);
   c->dxdn = std::pow(c->dxd, n);
+  c->dfac = std::pow(c->p.dx, 1.0 - n);
+  c->dfacd = std::pow(c->dxd, 1.0 - n);
   return LEM_OK;
 }
 

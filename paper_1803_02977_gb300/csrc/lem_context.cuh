@@ -39,7 +39,7 @@ struct lem_ctx {
   // Alg 6 for a general slope exponent (lem_set_slope_exponent); 0 updates =
   // the n = 1 closed form
   int newton_iters = 0;
-  double nexp = 1.0, neps = 0.0, dxn = 0.0, dxdn = 0.0;
+  double nexp = 1.0, neps = 0.0, dxn = 0.0, dxdn = 0.0, dfac = 0.0, dfacd = 0.0;
   // depression filling (lem_fill.cu): scratch allocated by the first flood
   int fill_on = 0;             // lem_step floods before every step
   int fill_grid = 0;           // co-resident blocks of the flood kernel
