@@ -71,6 +71,8 @@ def lib():
         L.orc_uplift.argtypes = [i32, i32, vp, pp]
         L.orc_erode.argtypes = [i32, i32, vp, vp, vp, vp, i64, vp, pp]
         L.orc_erode_newton.argtypes = [i32, i32, vp, vp, vp, vp, i64, vp, pp, dbl, dbl, i32]
+        L.orc_accumulate_mfd.argtypes = [i32, i32, vp, vp, dbl, vp, vp]
+        L.orc_accumulate_mfd.restype = i64
         L.orc_fill_eps.argtypes = [i32, i32, vp, vp]
         L.orc_fill_eps.restype = i32
         L.orc_fill_eps_f32.argtypes = [i32, i32, vp, vp]
@@ -208,6 +210,20 @@ def step(h, p, frozen_rec=None):
     uplift(hn, p)
     erode(hn, g.rec, g.queue, g.levels, g.cnt, p)
     return hn, g
+
+
+def accumulate_mfd(h, p=1.0, w=None):
+    """Eq. 2 with multiple flow directions on a (ny, nx) float64 array:
+    returns (A float64 (ny, nx), level int32 (ny, nx), number of levels)."""
+    ny, nx = h.shape
+    src = np.ascontiguousarray(h, np.float64)
+    wt = None if w is None else np.ascontiguousarray(w, np.float64).ravel()
+    A = np.zeros(nx * ny, np.float64)
+    lev = np.full(nx * ny, -1, np.int32)
+    L = lib().orc_accumulate_mfd(nx, ny, _p(src), _p(wt), float(p), _p(A), _p(lev))
+    if L < 0:
+        raise MemoryError("oracle allocation failed")
+    return A.reshape(ny, nx), lev.reshape(ny, nx), int(L)
 
 
 def fill(h):

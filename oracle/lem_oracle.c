@@ -223,6 +223,106 @@ void orc_erode_newton(int nx, int ny, double* h, const int32_t* rec, const int32
   }
 }
 
+/* ---- Multiple flow directions (Section "Multiple Flow Directions"; Eq. 2) - */
+/* Receivers of an interior cell: every strictly lower neighbour.  Its flow
+ * is split in proportion to slope^p (slope = (h_c - h_n) * w_k as in Alg 1),
+ * alpha(c -> n_k) = s_k^p / sum over receivers of s^p, the sum taken in k
+ * order.  Flow accumulation (Eq. 2): A(c) = w(c) + sum over the donors n of
+ * c, in k order of c's neighbours, of alpha(n -> c) * A(n), computed once
+ * every donor of c is final (cells taken level by level from those without
+ * donors). */
+
+static double orc_mfd_slope(const double* h, int64_t c, int64_t n, int k) {
+  double d = h[c] - h[n];
+  return orc_is_diagonal(k) ? d * ORC_INV_SQRT2 : d;
+}
+
+/* sum over c's receivers of slope^p, 0 without receivers */
+static double orc_mfd_norm(int nx, int ny, const double* h, int64_t c, double p) {
+  int x = (int)(c % nx), y = (int)(c / nx);
+  if (orc_on_perimeter(nx, ny, x, y)) return 0.0;
+  double sum = 0.0;
+  for (int k = 0; k < 8; ++k) {
+    int64_t n = (int64_t)(y + ORC_DY[k]) * nx + (x + ORC_DX[k]);
+    if (h[n] < h[c]) {
+      double s = orc_mfd_slope(h, c, n, k);
+      sum = sum + (p == 1.0 ? s : pow(s, p));
+    }
+  }
+  return sum;
+}
+
+int64_t orc_accumulate_mfd(int nx, int ny, const double* h, const double* w, double p,
+                           double* A, int32_t* level) {
+  int64_t n = (int64_t)nx * ny;
+  int32_t* pending = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int64_t* frontier = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  double* norm = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!pending || !frontier || !norm) {
+    free(pending);
+    free(frontier);
+    free(norm);
+    return -1;
+  }
+  /* donors of c: interior neighbours strictly above it */
+  for (int64_t c = 0; c < n; ++c) {
+    int x = (int)(c % nx), y = (int)(c / nx);
+    int cntd = 0;
+    for (int k = 0; k < 8; ++k) {
+      int xn = x + ORC_DX[k], yn = y + ORC_DY[k];
+      if (xn < 0 || yn < 0 || xn >= nx || yn >= ny) continue;
+      if (orc_on_perimeter(nx, ny, xn, yn)) continue;
+      if (h[(int64_t)yn * nx + xn] > h[c]) ++cntd;
+    }
+    pending[c] = cntd;
+    norm[c] = orc_mfd_norm(nx, ny, h, c, p);
+  }
+  /* level 0: cells without donors, ascending address */
+  int64_t head = 0, tail = 0;
+  for (int64_t c = 0; c < n; ++c)
+    if (pending[c] == 0) {
+      frontier[tail++] = c;
+      if (level) level[c] = 0;
+    }
+  int64_t nlevels = 0;
+  while (head < tail) {
+    int64_t end = tail;
+    ++nlevels;
+    for (; head < end; ++head) {
+      int64_t c = frontier[head];
+      int x = (int)(c % nx), y = (int)(c / nx);
+      /* Eq. 2, pulled from the donors in k order */
+      double a = w ? w[c] : 1.0;
+      for (int k = 0; k < 8; ++k) {
+        int xn = x + ORC_DX[k], yn = y + ORC_DY[k];
+        if (xn < 0 || yn < 0 || xn >= nx || yn >= ny) continue;
+        if (orc_on_perimeter(nx, ny, xn, yn)) continue;
+        int64_t d = (int64_t)yn * nx + xn;
+        if (!(h[d] > h[c])) continue;
+        /* the slope of the donor toward c: c is neighbour 7-k of d */
+        double s = orc_mfd_slope(h, d, c, 7 - k);
+        double alpha = (p == 1.0 ? s : pow(s, p)) / norm[d];
+        a = a + alpha * A[d];
+      }
+      A[c] = a;
+      /* release the receivers */
+      if (!orc_on_perimeter(nx, ny, x, y)) {
+        for (int k = 0; k < 8; ++k) {
+          int64_t r = (int64_t)(y + ORC_DY[k]) * nx + (x + ORC_DX[k]);
+          if (h[r] < h[c] && --pending[r] == 0) {
+            frontier[tail++] = r;
+            if (level) level[r] = (int32_t)nlevels;
+          }
+        }
+      }
+    }
+  }
+  free(pending);
+  free(frontier);
+  free(norm);
+  return nlevels;
+}
+
 /* ---- Depression filling before receivers (Section "Local Minima") -------- */
 /* Priority-Flood with epsilon increments: cells leave one priority queue in
  * order of their filled elevation w (ties by address), starting from the

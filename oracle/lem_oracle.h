@@ -107,6 +107,26 @@ void orc_erode_newton(int nx, int ny, double* h, const int32_t* rec, const int32
                       const int64_t* levels, int64_t nlevels, const int64_t* cnt,
                       const orc_params* p, double n_exp, double eps, int max_iter);
 
+/* Flow accumulation with multiple flow directions (Section "Multiple Flow
+ * Directions"; Eq. 2 with general alpha and w).  Receivers of an interior
+ * cell are all its strictly lower neighbours (perimeter cells and pits have
+ * none); cell c sends the fraction alpha(c -> n_k) = s_k^p / sum of s^p over
+ * its receivers (sum in k order), s_k = (h_c - h_n_k) * w_k as in Alg 1
+ * (Freeman's slope-weighted split; p = 1 is proportional to slope).
+ * A(c) = w(c) + sum over its donors d, in k order, of alpha(d -> c) * A(d);
+ * w NULL means w = 1.  Cells are taken level by level: level 0 are the cells
+ * without donors, a cell joins the level after its last donor's (Kahn's
+ * order on the donor graph, which the paper's figure on multiple flow
+ * directions requires: all of a cell's donors before it).  level (optional)
+ * receives each cell's level.  Returns the number of levels, or -1 on
+ * allocation failure.
+ * Pinned: dense linear solve (I - M^T) A = w on tiny grids; mass balance
+ * (the A of cells without receivers sum to the sum of w); a hand-computed
+ * 3x3 example; the level of every cell is one more than its deepest
+ * donor's. */
+int64_t orc_accumulate_mfd(int nx, int ny, const double* h, const double* w, double p,
+                           double* A, int32_t* level);
+
 /* Depression filling before Alg 1 (Section "Local Minima": fill depressions
  * to their outlets by Priority-Flood, resolving the resulting flats as part
  * of the flood).  w receives the least surface with w >= h, w = h on the
