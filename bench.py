@@ -365,6 +365,7 @@ def run_ours(args):
             vn = N / (float(np.mean(msn)) / 1e3)
             vd = N / (float(np.mean(msd)) / 1e3)
             forms["fill"] = measure_fill(lem, w, flush, dev, plain)
+            forms["mfd_accumulation"] = measure_mfd(lem, w, flush, dev)
             forms["slope_exponent_n2"] = {"workload": w.name, "n_hat": 2.0, "eps_m": 1e-12,
                                           "max_iter": 100, "ms_per_step": float(np.mean(msn)),
                                           "value": vn, "vs_plain_fp64": vn / plain,
@@ -534,6 +535,30 @@ def measure_fill(lem, w, flush, dev, plain, reps=5):
                                "device_wide": tiers[2]},
                 "ms_per_fill_and_step": step_ms, "value": N / (step_ms / 1e3),
                 "vs_plain_fp64": N / (step_ms / 1e3) / plain}}
+
+
+def measure_mfd(lem, w, flush, dev, reps=5, p=1.1):
+    """Flow accumulation with multiple flow directions (lem_accumulate_mfd,
+    Freeman's exponent 1.1) on workload w's initial surface: device time per
+    call with L2 flushed before it, and the number of levels."""
+    import torch
+    h = torch.tensor(w.initial(), device=dev)
+    mdl = lem.Model(h, dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt)
+    A = torch.empty_like(h)
+    stream = torch.cuda.current_stream()
+    ms, L = [], 0
+    for r in range(reps + 2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L = lem.lem_accumulate_mfd(mdl.ctx, A, p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r >= 2:
+            ms.append(e0.elapsed_time(e1))
+    mdl.close()
+    t = float(np.median(ms))
+    return {"workload": w.name, "p": p, "ms": t, "levels": L, "cells_per_s": w.cells / (t / 1e3)}
 
 
 def measure_batch(lem, steps, ws, rank, dev, count=512, sample_every=8):

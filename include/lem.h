@@ -138,6 +138,31 @@ LEM_API int lem_levels(lem_ctx* ctx, int64_t* nlevels, int32_t* dev_queue, int64
  * count width (int32 or int64).  Requires lem_levels. */
 LEM_API int lem_accumulate(lem_ctx* ctx, void* dev_counts);
 
+/* Flow accumulation with multiple flow directions (Section "Multiple Flow
+ * Directions"; Eq. 2 with a general split alpha and source w), from the
+ * bound elevations.  Receivers of an interior cell are all its strictly
+ * lower neighbours (perimeter cells and pits have none); cell d sends
+ *     alpha(d -> n_k) = s_k^p / (sum over its receivers of s^p),
+ * s_k = (h_d - h_n_k) * w_k with Alg 1's weights (1 cardinal, the double
+ * nearest 1/sqrt2 diagonal), the sum in k order (Freeman's slope-weighted
+ * split; p = 1 is proportional to slope, large p approaches steepest
+ * descent).  Then A(c) = w(c) + sum over the donors d of c, in k order of
+ * c's neighbours, of alpha(d -> c) * A(d), in FP64 with each operation
+ * rounded separately, every donor before its receivers (Kahn's levels on
+ * the donor graph, which multiple flow directions require).  A does not
+ * depend on the order of cells within a level; for p = 1 it is bit-exact
+ * against a serial evaluation.
+ *  p          split exponent, > 0 and finite
+ *  dev_w      nx*ny doubles of source w(c), or NULL for 1 per cell (A then
+ *             in cells; scale by dx*dx for area)
+ *  dev_A      nx*ny doubles receiving A
+ *  nlevels    if not NULL, receives the number of levels
+ * The D8 stages (receivers, levels, counts, erosion) are not affected.  The
+ * first call allocates 16 bytes of scratch per cell.  Synchronises the
+ * stream. */
+LEM_API int lem_accumulate_mfd(lem_ctx* ctx, double p, const double* dev_w, double* dev_A,
+                               int64_t* nlevels);
+
 /* Alg 5 + Alg 6 (Steps 6-7) for n-hat = 1, fused: interior cells without a
  * receiver are uplifted, h += dt*U; then, level 1 upward, every cell takes
  * h = (h + dt*U + F*h_r) / (1 + F), F = K*dt*(count*area_scale)^m / d,

@@ -444,6 +444,10 @@ void lem_destroy(lem_ctx* c) {
   cudaFree(c->fill_dirty);
   cudaFree(c->fill_state);
   cudaFree(c->fill_ptr);
+  cudaFree(c->mfd_pending);
+  cudaFree(c->mfd_norm);
+  cudaFree(c->mfd_queue);
+  cudaFree(c->mfd_state);
   if (c->host_status) cudaFreeHost(c->host_status);
   delete c;
 }

@@ -46,6 +46,13 @@ struct lem_ctx {
   void* fill_w = nullptr;      // relaxed surface, nx*ny elements
   uint8_t* fill_dirty = nullptr;  // two per-tile flag arrays
   int* fill_ptr = nullptr;     // chain pointers, nx*ny
+  // flow accumulation with multiple flow directions (lem_mfd.cu): scratch
+  // allocated by the first call
+  int mfd_grid = 0;
+  int* mfd_pending = nullptr;  // donors not yet computed, nx*ny
+  double* mfd_norm = nullptr;  // receivers' sum of slope^p, nx*ny
+  int* mfd_queue = nullptr;    // the levels, nx*ny
+  void* mfd_state = nullptr;
   void* fill_state = nullptr;  // round counters
   double wait_limit_s = 2.0;
   unsigned long long* trace = nullptr;  // device trace buffer (lem_trace_enable)

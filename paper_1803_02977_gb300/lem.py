@@ -50,6 +50,7 @@ SIGNATURES = [
     ("lem_erode", _I, [_VP]),
     ("lem_step", _I, [_VP, _I]),
     ("lem_set_slope_exponent", _I, [_VP, _D, _D, _I]),
+    ("lem_accumulate_mfd", _I, [_VP, _D, _VP, _VP, _I64P]),
     ("lem_fill", _I, [_VP]),
     ("lem_set_fill", _I, [_VP, _I]),
     ("lem_fill_stats", _I, [_VP, _I64P]),
@@ -177,6 +178,15 @@ def lem_step(ctx, nsteps):
 
 def lem_set_slope_exponent(ctx, n, eps=1e-12, max_iter=100):
     _check(lib().lem_set_slope_exponent(ctx, n, eps, max_iter), "lem_set_slope_exponent")
+
+
+def lem_accumulate_mfd(ctx, A, p=1.0, w=None):
+    """Eq. 2 with multiple flow directions into the float64 tensor A;
+    returns the number of levels."""
+    L = ctypes.c_int64(0)
+    _check(lib().lem_accumulate_mfd(ctx, p, _ptr(w), _ptr(A), ctypes.byref(L)),
+           "lem_accumulate_mfd")
+    return L.value
 
 
 def lem_fill(ctx):
@@ -438,6 +448,13 @@ class Model:
 
     def fill(self):
         lem_fill(self.ctx)
+
+    def accumulate_mfd(self, p=1.0, w=None):
+        """(A, number of levels) of Eq. 2 with multiple flow directions."""
+        A = torch.empty(self.ny, self.nx, dtype=torch.float64, device=self.h.device)
+        wt = None if w is None else w.to(torch.float64).contiguous()
+        L = lem_accumulate_mfd(self.ctx, A, p, wt)
+        return A, L
 
     def set_fill(self, on):
         lem_set_fill(self.ctx, on)
