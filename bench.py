@@ -685,16 +685,24 @@ def traced_step(lem, mdl, flush, nsteps=3):
             "steps_in_launch": nsteps, "raw": raw}
 
 
+STEP_KERNEL_SOURCES = ("lem_step_kernel.cuh", "lem_tiles.cuh", "lem_device.cuh",
+                       "lem_context.cuh", "lem_api.cu")
+
+
 def kernel_source_hash():
-    """sha256 over the kernel sources and the C-ABI header (name + bytes,
-    in sorted order); a committed ncu summary records the hash it was taken
-    at, so its DRAM figures are only reported while the kernels match."""
+    """sha256 over what the step kernel and its launch are built from (its
+    device sources, the translation unit that launches it and the compiler
+    flags; name + bytes in order); a committed ncu summary records the hash
+    it was taken at, so its DRAM figures are only reported while the kernel
+    matches."""
+    from paper_1803_02977_gb300 import build as b
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_1803_02977_gb300", "csrc", "*.cu*")))
-    for p in files + [os.path.join(ROOT, "include", "lem.h")]:
+    csrc = os.path.join(ROOT, "paper_1803_02977_gb300", "csrc")
+    for p in [os.path.join(csrc, n) for n in STEP_KERNEL_SOURCES]:
         h.update(os.path.basename(p).encode())
         with open(p, "rb") as f:
             h.update(f.read())
+    h.update(" ".join(b.ARCH + [f for f in b.NVCC_FLAGS if not f.startswith("/")]).encode())
     return h.hexdigest()
 
 
