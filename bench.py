@@ -538,27 +538,31 @@ def measure_fill(lem, w, flush, dev, plain, reps=5):
 
 
 def measure_mfd(lem, w, flush, dev, reps=5, p=1.1):
-    """Flow accumulation with multiple flow directions (lem_accumulate_mfd,
-    Freeman's exponent 1.1) on workload w's initial surface: device time per
-    call with L2 flushed before it, and the number of levels."""
+    """Flow accumulation with multiple flow directions (lem_accumulate_mfd)
+    on workload w's initial surface, with Freeman's exponent p and with
+    p = 1 (no powers): device time per call with L2 flushed before it, and
+    the number of levels."""
     import torch
     h = torch.tensor(w.initial(), device=dev)
     mdl = lem.Model(h, dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt)
     A = torch.empty_like(h)
     stream = torch.cuda.current_stream()
-    ms, L = [], 0
-    for r in range(reps + 2):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        L = lem.lem_accumulate_mfd(mdl.ctx, A, p)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if r >= 2:
-            ms.append(e0.elapsed_time(e1))
+    out = {"workload": w.name}
+    for key, pe in (("p", p), ("p1", 1.0)):
+        ms, L = [], 0
+        for r in range(reps + 2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L = lem.lem_accumulate_mfd(mdl.ctx, A, pe)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r >= 2:
+                ms.append(e0.elapsed_time(e1))
+        t = float(np.median(ms))
+        out[key] = {"p": pe, "ms": t, "levels": L, "cells_per_s": w.cells / (t / 1e3)}
     mdl.close()
-    t = float(np.median(ms))
-    return {"workload": w.name, "p": p, "ms": t, "levels": L, "cells_per_s": w.cells / (t / 1e3)}
+    return out
 
 
 def measure_batch(lem, steps, ws, rank, dev, count=512, sample_every=8):
