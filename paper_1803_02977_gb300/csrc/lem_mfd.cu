@@ -63,7 +63,12 @@ __device__ __forceinline__ double mfd_slope(double hi, double lo, int k) {
   return nbr_diag(k) ? __dmul_rn(d, kInvSqrt2) : d;
 }
 
-__device__ __forceinline__ double mfd_pow(double s, double p) { return p == 1.0 ? s : pow(s, p); }
+// s^p for a positive slope s, as 2^(p log2 s): two FP64 library calls
+// instead of the costlier general power, within a few units in the last
+// place of it for the slopes of a grid (|p log2 s| well below 2^10)
+__device__ __forceinline__ double mfd_pow(double s, double p) {
+  return p == 1.0 ? s : exp2(p * log2(s));
+}
 
 // Append the lanes' flagged cells to the queue (one atomic per warp).
 __device__ __forceinline__ void mfd_append(int* queue, int* tail, bool f, int c) {
