@@ -434,11 +434,11 @@ def run_ours(args):
     return 0
 
 
-def time_grid(lem, w, steps, warmup, flush, dev, slope_exponent=None, mode=None, fill=False):
+def time_grid(lem, w, steps, warmup, flush, dev, slope_exponent=None, mode=None):
     """Per-step device times (ms) of `steps` single-step lem_step calls on
     workload w, L2 flushed between steps.  slope_exponent: Alg 6's Newton
     form with that n-hat (eps 1e-12 m, at most 100 updates); mode: the
-    lem_set_step_mode form; fill: depression filling before every step."""
+    lem_set_step_mode form."""
     import torch
     P = 8 if w.dtype == "f64" else 4
     count_bits = 64 if w.area_dtype == "i64" else 32
@@ -448,8 +448,6 @@ def time_grid(lem, w, steps, warmup, flush, dev, slope_exponent=None, mode=None,
         mdl.set_slope_exponent(slope_exponent, 1e-12, 100)
     if mode is not None:
         lem.lem_set_step_mode(mdl.ctx, mode)
-    if fill:
-        mdl.set_fill(True)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         mdl.step(1)
