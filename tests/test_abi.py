@@ -71,3 +71,15 @@ def test_algorithmic_bytes_match_the_roofline_table():
     assert sum(bench.algo_bytes(8, 4).values()) == 66   # FP64 elevations, int32 counts
     assert sum(bench.algo_bytes(4, 4).values()) == 50   # FP32, int32
     assert sum(bench.algo_bytes(4, 8).values()) == 62   # FP32, int64
+
+
+def test_new_entry_points_reject_null_context_without_device_work(lib):
+    # answered on the host: no context, so no device memory is touched
+    from paper_1803_02977_gb300 import lem
+    c_d, c_i, c_vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+    assert lib.lem_set_slope_exponent(None, c_d(2.0), c_d(1e-12), c_i(10)) == lem.LEM_EINVAL
+    assert lib.lem_fill(None) == lem.LEM_EINVAL
+    assert lib.lem_set_fill(None, c_i(1)) == lem.LEM_EINVAL
+    stats = (ctypes.c_int64 * 4)()
+    assert lib.lem_fill_stats(None, stats) == lem.LEM_EINVAL
+    assert lib.lem_accumulate_mfd(None, c_d(1.0), None, c_vp(0), None) == lem.LEM_EINVAL
