@@ -358,19 +358,15 @@ def run_ours(args):
             v32 = N / (float(np.mean(ms32)) / 1e3)
             forms["fp32_same_grid"] = {"workload": "grid2048_f32", "ms_per_step": float(np.mean(ms32)),
                                        "value": v32, "vs_plain_fp64": v32 / plain}
-            # Alg 6 with n-hat = 2 (Newton sweep on device-wide levels), next to
-            # the n-hat = 1 step on the same device-wide levels (mode 1)
-            msn = time_grid(lem, w, min(K, 20), 3, flush, dev, slope_exponent=2.0)
-            msd = time_grid(lem, w, min(K, 20), 3, flush, dev, mode=1)
-            vn = N / (float(np.mean(msn)) / 1e3)
-            vd = N / (float(np.mean(msd)) / 1e3)
             forms["fill"] = measure_fill(lem, w, flush, dev, plain)
             forms["mfd_accumulation"] = measure_mfd(lem, w, flush, dev)
-            forms["slope_exponent_n2"] = {"workload": w.name, "n_hat": 2.0, "eps_m": 1e-12,
-                                          "max_iter": 100, "ms_per_step": float(np.mean(msn)),
-                                          "value": vn, "vs_plain_fp64": vn / plain,
-                                          "device_wide_n1": {"ms_per_step": float(np.mean(msd)),
-                                                             "value": vd}}
+            # Alg 6 with n-hat = 2 and 1.5 (Newton-Raphson in every tier)
+            for nh in (2.0, 1.5):
+                msn = time_grid(lem, w, min(K, 20), 3, flush, dev, slope_exponent=nh)
+                vn = N / (float(np.mean(msn)) / 1e3)
+                forms[f"slope_exponent_n{nh:g}"] = {
+                    "workload": w.name, "n_hat": nh, "eps_m": 1e-12, "max_iter": 100,
+                    "ms_per_step": float(np.mean(msn)), "value": vn, "vs_plain_fp64": vn / plain}
         w10 = synth.workload("grid10000_f32")
         ms10 = time_grid(lem, w10, 5, 2, flush, dev)
         a10 = sum(algo_bytes(4, 8).values()) * w10.cells / (float(np.mean(ms10)) / 1e3) / 1e9

@@ -170,16 +170,16 @@ LEM_API int lem_accumulate_mfd(lem_ctx* ctx, double p, const double* dev_w, doub
  * updated elevation.  The update is evaluated in the algebraically identical
  * increment form h0 - g*(h0 - h_r), h0 = h + dt*U, g = F/(1+F) from a table
  * computed in FP64 (rounded once to float for FP32 contexts); FP64 results
- * are within a few units in the last place of the closed form.
+ * are within a few units in the last place of the closed form.  With a
+ * slope exponent other than 1 (lem_set_slope_exponent) each cell's update is
+ * Alg 6's Newton-Raphson iteration instead.
  * Updates the bound elevations in place.  Requires lem_accumulate. */
 LEM_API int lem_erode(lem_ctx* ctx);
 
 /* "Rinse, Repeat": nsteps full time steps (receivers through erosion) in
  * one cooperative persistent launch with device-wide barriers between
- * levels; no host round trip between levels or steps.  With a slope
- * exponent other than 1 (lem_set_slope_exponent) each step is two
- * cooperative launches: Algs 1-4 on device-wide levels, then the Newton
- * sweep of Alg 6. */
+ * levels; no host round trip between levels or steps.  With depression
+ * filling on (lem_set_fill) each step is a flood launch and a step launch. */
 LEM_API int lem_step(lem_ctx* ctx, int nsteps);
 
 /* Alg 6 (Step 7) for a general slope exponent n-hat (Eq. 1, erosion rate
@@ -201,10 +201,10 @@ LEM_API int lem_step(lem_ctx* ctx, int nsteps);
  *            ignored.
  *  eps       tolerance in metres, finite and > 0
  *  max_iter  1 .. 1000
- * Returns LEM_EINVAL for other values.  While n != 1, lem_step runs Algs 3-6
- * on device-wide levels for every step (lem_set_step_mode's private tiers
- * evaluate only n = 1) and lem_adjoint returns LEM_EINVAL.  Takes effect at
- * the next launch; no device work. */
+ * Returns LEM_EINVAL for other values.  While n != 1 the step kernel's own
+ * instantiation for the general exponent runs, in every tier and stage
+ * call, and lem_adjoint returns LEM_EINVAL.  Takes effect at the next
+ * launch; no device work. */
 LEM_API int lem_set_slope_exponent(lem_ctx* ctx, double n, double eps, int max_iter);
 
 /* Depression filling before Alg 1 (Section "Local Minima": depressions

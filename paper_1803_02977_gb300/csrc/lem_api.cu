@@ -18,8 +18,6 @@
 
 using namespace lem;
 
-template <typename HT, typename CT>
-int lem_newton_launch(const StepArgs<HT, CT>& a, int grid, cudaStream_t stream);
 int lem_fill_launch(lem_ctx* c);
 
 
@@ -137,14 +135,18 @@ __global__ void selftest_wait_kernel(DevState* st) {
 }
 
 template <typename HT, typename CT>
-const void* step_kernel_ptr() {
-  return (const void*)&lem_step_kernel<HT, CT>;
+const void* step_kernel_ptr(bool newton) {
+  return newton ? (const void*)&lem_step_kernel<HT, CT, true>
+                : (const void*)&lem_step_kernel<HT, CT, false>;
 }
 
-const void* kernel_for(const lem_ctx* c) {
+// The step kernel of a context's element and count types; newton: the
+// instantiation for a general slope exponent.
+const void* kernel_for(const lem_ctx* c, bool newton) {
   const bool f64 = c->p.dtype == LEM_F64, c64 = c->p.count_bits == 64;
-  if (f64) return c64 ? step_kernel_ptr<double, long long>() : step_kernel_ptr<double, int>();
-  return c64 ? step_kernel_ptr<float, long long>() : step_kernel_ptr<float, int>();
+  if (f64) return c64 ? step_kernel_ptr<double, long long>(newton)
+                      : step_kernel_ptr<double, int>(newton);
+  return c64 ? step_kernel_ptr<float, long long>(newton) : step_kernel_ptr<float, int>(newton);
 }
 
 template <typename HT, typename CT>
@@ -201,23 +203,9 @@ template <typename HT, typename CT>
 int launch_typed(lem_ctx* c, int phases, int nsteps) {
   StepArgs<HT, CT> a = make_args<HT, CT>(c, phases, nsteps);
   void* args[] = {&a};
-  LEM_CUDA(cudaLaunchCooperativeKernel(step_kernel_ptr<HT, CT>(), dim3(c->grid), dim3(kBD), args,
-                                       kDynSmem, c->stream));
+  LEM_CUDA(cudaLaunchCooperativeKernel(step_kernel_ptr<HT, CT>(c->newton_iters > 0), dim3(c->grid),
+                                       dim3(kBD), args, kDynSmem, c->stream));
   return LEM_OK;
-}
-
-// Alg 6 for a general slope exponent: its own cooperative kernel
-// (lem_newton.cu) over the device-wide levels of the last levels phase.
-template <typename HT, typename CT>
-int launch_newton_typed(lem_ctx* c) {
-  const StepArgs<HT, CT> a = make_args<HT, CT>(c, kPhEro, 1);
-  return lem_newton_launch<HT, CT>(a, c->grid, c->stream);
-}
-
-int launch_newton(lem_ctx* c) {
-  const bool f64 = c->p.dtype == LEM_F64, c64 = c->p.count_bits == 64;
-  if (f64) return c64 ? launch_newton_typed<double, long long>(c) : launch_newton_typed<double, int>(c);
-  return c64 ? launch_newton_typed<float, long long>(c) : launch_newton_typed<float, int>(c);
 }
 
 int launch_step(lem_ctx* c, int phases, int nsteps) {
@@ -368,11 +356,18 @@ int lem_create_ex(lem_ctx** out, const lem_params* pin) {
   const size_t N = (size_t)c->N;
   int nsm = 0, per_sm = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kernel_for(c), cudaFuncAttributeMaxDynamicSharedMemorySize,
+  for (int nw = 0; nw < 2 && e == cudaSuccess; ++nw)
+    e = cudaFuncSetAttribute(kernel_for(c, nw != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kDynSmem);
+  // both instantiations are launched with this grid: it must suit either
+  int per_sm_newton = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(c), kBD, kDynSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(c, false), kBD,
+                                                      kDynSmem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_newton, kernel_for(c, true), kBD,
+                                                      kDynSmem);
+  if (e == cudaSuccess && per_sm_newton < per_sm) per_sm = per_sm_newton;
   if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
   if (e == cudaSuccess) {
     c->grid = nsm * (per_sm < 2 ? per_sm : 2);
@@ -546,7 +541,7 @@ int lem_erode(lem_ctx* c) {
   if (!c) return LEM_EINVAL;
   if (!c->h) return LEM_ESTATE;
   if (!c->acc_valid) return LEM_ESTATE;
-  int rc = c->newton_iters > 0 ? launch_newton(c) : launch_step(c, kPhEro, 1);
+  int rc = launch_step(c, kPhEro, 1);
   if (rc != LEM_OK) return rc;
   if (!c->frozen) c->rec_valid = c->lev_valid = c->acc_valid = false;
   return LEM_OK;
@@ -556,26 +551,15 @@ int lem_step(lem_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return LEM_EINVAL;
   if (!c->h) return LEM_ESTATE;
   if (nsteps == 0) return LEM_OK;
-  if (c->newton_iters > 0 || c->fill_on) {
-    // one step at a time: the depression flood first (lem_set_fill), then
-    // either the step kernel or, for a general slope exponent, Algs 1-4 on
-    // device-wide levels and the Newton sweep
+  if (c->fill_on) {
+    // one step at a time: the depression flood, then the step
     for (int s = 0; s < nsteps; ++s) {
-      int rc = LEM_OK;
-      if (c->fill_on) {
-        rc = lem_fill_launch(c);
-        if (rc != LEM_OK) return rc;
-      }
-      if (c->newton_iters > 0) {
-        rc = launch_step(c, kPhRec | kPhLev | kPhAcc, 1);
-        if (rc == LEM_OK) rc = launch_newton(c);
-      } else {
-        rc = launch_step(c, c->mode == 0 ? kPhTiles : kPhAll, 1);
-      }
+      int rc = lem_fill_launch(c);
+      if (rc == LEM_OK) rc = launch_step(c, c->mode == 0 ? kPhTiles : kPhAll, 1);
       if (rc != LEM_OK) return rc;
     }
     c->rec_valid = c->frozen;
-    c->lev_valid = c->acc_valid = c->frozen && (c->newton_iters > 0 || c->mode == 1);
+    c->lev_valid = c->acc_valid = c->frozen && c->mode == 1;
     return LEM_OK;
   }
   int rc = launch_step(c, c->mode == 0 ? kPhTiles : kPhAll, nsteps);

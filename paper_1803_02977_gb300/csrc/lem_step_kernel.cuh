@@ -554,14 +554,35 @@ __device__ __forceinline__ HT erode_value(const StepArgs<HT, CT>& a, int c, int 
 // updates.  FP64 for either elevation type.  For n >= 1, f is convex and
 // increasing above hr, so the iterates fall monotonically to the root and
 // stay above hr.  A cell whose h0 is not above hr keeps h0: the power of a
-// non-positive slope is undefined for non-integer n.  Kept out of line so
-// that the n = 1 loops around it are compiled as before.
+// non-positive slope is undefined for non-integer n.  The step kernel has an
+// instantiation of its own for it (lem_step_kernel<HT, CT, true>), so the
+// n = 1 kernel is compiled without it.
+// The Newton-Raphson iteration of Alg 6 for one cell: the root of
+// h - h0 + F*(h - hr)^n from h = h0; h0 itself if it is not above hr.
+static __device__ __noinline__ double newton_solve(double h0, double hr, double F, double n,
+                                                   double eps,
+                                            int iters) {
+  if (!(h0 - hr > 0.0)) return h0;
+  double hn = h0, hp = h0;
+  for (int it = 0; it < iters; ++it) {
+    const double x = hn - hr;
+    // x^(n-1), as 2^((n-1) log2 x): two FP64 library calls instead of the
+    // costlier general power, within a few units in the last place of it
+    const double p = (n == 2.0) ? x : exp2((n - 1.0) * log2(x));
+    const double f = (hn - h0) + F * (p * x);
+    const double fp = 1.0 + F * n * p;
+    hn = hn - f / fp;
+    const double d = hn - hp;
+    hp = hn;
+    if (!(fabs(d) > eps)) break;
+  }
+  return hn;
+}
+
 template <typename HT, typename CT>
-__device__ __noinline__ HT erode_newton(const StepArgs<HT, CT>& a, int c, int k, CT count,
-                                        HT hcur, HT hrecv) {
-  const double hr = (double)hrecv;
+__device__ __forceinline__ HT erode_newton(const StepArgs<HT, CT>& a, int c, int k, CT count,
+                                           HT hcur, HT hrecv) {
   const double h0 = (double)hcur + uplift_dt(a, c);
-  if (!(h0 - hr > 0.0)) return (HT)h0;
   // F = K*dt*A^m / d^n: for tabulated counts the n = 1 factor times d^(1-n)
   const bool diag = nbr_diag(k);
   double F;
@@ -571,19 +592,7 @@ __device__ __noinline__ HT erode_newton(const StepArgs<HT, CT>& a, int c, int k,
     const double A = (double)count * a.area_scale;
     F = a.Kdt * pow(A, a.m) / (diag ? a.dxdn : a.dxn);
   }
-  const double n = a.nexp;
-  double hn = h0, hp = h0;
-  for (int it = 0; it < a.newton_iters; ++it) {
-    const double x = hn - hr;
-    const double p = (n == 2.0) ? x : pow(x, n - 1.0);  // x^(n-1)
-    const double f = (hn - h0) + F * (p * x);
-    const double fp = 1.0 + F * n * p;
-    hn = hn - f / fp;
-    const double d = hn - hp;
-    hp = hn;
-    if (!(fabs(d) > a.neps)) break;
-  }
-  return (HT)hn;
+  return (HT)newton_solve(h0, (double)hrecv, F, a.nexp, a.neps, a.newton_iters);
 }
 
 // Erode up to kItems cells (entries < 0 are skipped) with all loads issued
@@ -1383,7 +1392,7 @@ __device__ __noinline__ bool phase_global_erode(const StepArgs<HT, CT>& a, int L
 // in pqm and receiver codes in pqk.  Returns the number of cells handled, or
 // -1 if the forest outgrows the region (pcap entries, kMaxPrivLevels levels);
 // then nothing was eroded.  Block barriers only.
-template <typename HT, typename CT>
+template <typename HT, typename CT, bool kNewton = false>
 __device__ __noinline__ int private_forest(const StepArgs<HT, CT>& a, Shared& s, int n0) {
   const int b = blockIdx.x, t = threadIdx.x;
   const int nx = a.nx;
@@ -1588,8 +1597,15 @@ __device__ __noinline__ int private_forest(const StepArgs<HT, CT>& a, Shared& s,
         }
       }
 #pragma unroll
-      for (int i = 0; i < kItems; ++i)
-        if (cs[i] >= 0) a.h[cs[i]] = erode_value(a, cs[i], ks[i], ns[i], hc[i], hr[i]);
+      for (int i = 0; i < kItems; ++i) {
+        if (cs[i] >= 0) {
+          if constexpr (kNewton) {
+            a.h[cs[i]] = erode_newton(a, cs[i], ks[i], ns[i], hc[i], hr[i]);
+          } else {
+            a.h[cs[i]] = erode_value(a, cs[i], ks[i], ns[i], hc[i], hr[i]);
+          }
+        }
+      }
     }
     __syncthreads();
   }
@@ -1602,7 +1618,9 @@ __device__ __noinline__ int private_forest(const StepArgs<HT, CT>& a, Shared& s,
 
 namespace lem {
 
-template <typename HT, typename CT>
+// kNewton: Alg 6 for a general slope exponent (newton_solve) in every tier
+// in place of the n = 1 closed form.
+template <typename HT, typename CT, bool kNewton = false>
 __global__ void __launch_bounds__(kBD, 1) lem_step_kernel(const __grid_constant__ StepArgs<HT, CT> a) {
   __shared__ Shared s;
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
@@ -1623,7 +1641,8 @@ __global__ void __launch_bounds__(kBD, 1) lem_step_kernel(const __grid_constant_
         a.st->dev_roots[par ^ 1] = 0;
         a.st->covered[par ^ 1] = 0;
       }
-      phase_tiles(a, s, &a.st->tiles_next[par], &a.st->dev_roots[par], &a.st->covered[par]);
+      phase_tiles<HT, CT, kNewton>(a, s, &a.st->tiles_next[par], &a.st->dev_roots[par],
+                                   &a.st->covered[par]);
       if (!grid_barrier(a.st, gridDim.x)) return;
       trace_point(a.st, kTrTilesEnd);
       if (lead) a.st->tiles_next[par] = 0;  // every block has stopped claiming
@@ -1636,7 +1655,7 @@ __global__ void __launch_bounds__(kBD, 1) lem_step_kernel(const __grid_constant_
         const int L = phase_global_levels(a, s, dr, false);
         if (L < 0) return;
         if (!phase_global_accumulate(a, L)) return;
-        if (!phase_global_erode(a, L)) return;  // ends with a grid barrier
+        if (!phase_global_erode<HT, CT, kNewton>(a, L)) return;  // ends with a grid barrier
         if (lead) {
           a.st->covered[par] += a.levels[L];
           a.st->tier_cells[2] += (unsigned long long)a.levels[L];
@@ -1660,7 +1679,7 @@ __global__ void __launch_bounds__(kBD, 1) lem_step_kernel(const __grid_constant_
     if (a.phases & (kPhAcc | kPhEro)) {
       if (L < 0) L = ld_volatile(&a.st->nlevels);
       if ((a.phases & kPhAcc) && !phase_global_accumulate(a, L)) return;
-      if ((a.phases & kPhEro) && !phase_global_erode(a, L)) return;
+      if ((a.phases & kPhEro) && !phase_global_erode<HT, CT, kNewton>(a, L)) return;
     }
   }
 }

@@ -108,13 +108,19 @@ __device__ __forceinline__ void push_tile_roots_device(const uint8_t* code, int*
 // Erosion parameters of the warp tier, copied out of the kernel parameter
 // once per tile so that stores to h do not force them to be reloaded.  All
 // of a warp forest's counts are below kTableN: g always comes from a table.
-template <typename HT>
+template <typename HT, bool kNewton = false>
 struct TileErode {
   const void* gtab;  // F/(1+F): double2 {F, g} (FP64) or float (FP32); diagonal at +tn
   int tn;            // counts tabulated (every warp-forest count is below it)
   const double* Uf;
   double Udt, dt;
   float Udt_f;
+  // Alg 6 for a general slope exponent (kNewton): the {F, g} table (for
+  // either elevation type), d^(1-n) for cardinal and diagonal receivers,
+  // the exponent, the tolerance and the update limit
+  const double2* Ftab;
+  double dfac, dfacd, nexp, neps;
+  int iters;
   // Alg 5: h + dt*U (the same operations as uplift_sink)
   __device__ __forceinline__ HT uplift(int c, HT hcur) const {
     if constexpr (sizeof(HT) == 8) {
@@ -125,7 +131,12 @@ struct TileErode {
   }
   __device__ __forceinline__ HT operator()(int c, int k, unsigned count, HT hcur, HT hr) const {
     const int i = (nbr_diag(k) ? tn : 0) + (int)count;
-    if constexpr (sizeof(HT) == 8) {
+    if constexpr (kNewton) {
+      // the operations of erode_newton for a tabulated count
+      const double h0 = (double)hcur + (Uf ? __dmul_rn(Uf[c], dt) : Udt);
+      const double F = Ftab[i].x * (nbr_diag(k) ? dfacd : dfac);
+      return (HT)newton_solve(h0, (double)hr, F, nexp, neps, iters);
+    } else if constexpr (sizeof(HT) == 8) {
       const double g = static_cast<const double2*>(gtab)[i].y;
       const double h0 = __dadd_rn(hcur, Uf ? __dmul_rn(Uf[c], dt) : Udt);
       return __fma_rn(-g, __dsub_rn(h0, hr), h0);
@@ -139,20 +150,20 @@ struct TileErode {
 
 // What a warp forest reads: the grid, its codes and masks (Algs 1-2 done),
 // the elevations it erodes and the erosion parameters.
-template <typename HT>
+template <typename HT, bool kNewton = false>
 struct TileArgs {
   int nx, ny, tiles_x;
   const uint8_t* code;
   const uint8_t* mask;
   HT* h;
-  TileErode<HT> ero;
+  TileErode<HT, kNewton> ero;
 };
 
 // Algs 3-6 on the trees rooted in work item `item` (tile_item), by one warp.
 // off[k] is the address offset of neighbour k.  Returns the number of cells
 // handled, or -1 if the forest does not fit (nothing was written).
-template <typename HT>
-__device__ __forceinline__ int tile_forest(const TileArgs<HT>& a, const TileQ<HT>& q,
+template <typename HT, bool kNewton>
+__device__ __forceinline__ int tile_forest(const TileArgs<HT, kNewton>& a, const TileQ<HT>& q,
                                            const int* off, int item, int lane) {
   using Q = TileQ<HT>;
   // the arguments used in the loops, held in registers (stores through other
@@ -277,7 +288,7 @@ __device__ __forceinline__ int tile_forest(const TileArgs<HT>& a, const TileQ<HT
   }
   cp_async_wait_all();  // every entry's elevation has arrived
   __syncwarp();
-  const TileErode<HT> ero = a.ero;
+  const TileErode<HT, kNewton> ero = a.ero;
   HT* const hh = a.h;
   // Alg 5 on level 0: pits are uplifted, the perimeter stays
   for (int jj = lane; jj < n; jj += 32) {
@@ -307,7 +318,7 @@ __device__ __forceinline__ int tile_forest(const TileArgs<HT>& a, const TileQ<HT
 // The block tier: level 0 = the roots of this block's nov overflowed tiles
 // (s.ovf_tiles).  Returns the number of cells handled, or 0 after handing
 // the roots to the device tier when the block's queue cannot hold them.
-template <typename HT, typename CT>
+template <typename HT, typename CT, bool kNewton>
 __device__ __noinline__ int block_tier(const StepArgs<HT, CT>& a, Shared& s, int nov,
                                        int* dev_roots) {
   const int b = blockIdx.x, t = threadIdx.x, w = t >> 5, lane = t & 31;
@@ -339,7 +350,7 @@ __device__ __noinline__ int block_tier(const StepArgs<HT, CT>& a, Shared& s, int
   }
   __syncthreads();
   const int n0 = s.n0;
-  const int done = (n0 <= a.pcap) ? private_forest(a, s, n0) : -1;
+  const int done = (n0 <= a.pcap) ? private_forest<HT, CT, kNewton>(a, s, n0) : -1;
   if (done >= 0) return done;
   for (int i = w; i < nov; i += kWarps)
     push_tile_roots_device<TH>(a.code, a.queue, dev_roots, s.ovf_tiles[i], a.tiles_x, nx, ny,
@@ -351,7 +362,7 @@ __device__ __noinline__ int block_tier(const StepArgs<HT, CT>& a, Shared& s, int
 // tiles.  Roots that neither tier can hold are appended to the device tier's
 // level 0 (queue, counter *dev_roots).  The cells handled are added to
 // *covered and to the per-tier totals.
-template <typename HT, typename CT>
+template <typename HT, typename CT, bool kNewton>
 __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, int* tiles_next,
                                          int* dev_roots, int* covered) {
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
@@ -363,7 +374,7 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
   }
   if (t < 8) s.off[t] = nbr_off(t, a.nx);
   __syncthreads();
-  TileArgs<HT> ta;
+  TileArgs<HT, kNewton> ta;
   ta.nx = a.nx;
   ta.ny = a.ny;
   ta.tiles_x = a.tiles_x;
@@ -380,6 +391,14 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
   ta.ero.Udt = a.Udt;
   ta.ero.dt = a.dt;
   ta.ero.Udt_f = a.Udt_f;
+  if constexpr (kNewton) {
+    ta.ero.Ftab = a.Ftab;
+    ta.ero.dfac = a.dfac;
+    ta.ero.dfacd = a.dfacd;
+    ta.ero.nexp = a.nexp;
+    ta.ero.neps = a.neps;
+    ta.ero.iters = a.newton_iters;
+  }
   long long mine = 0;
   // work items are claimed one at a time from a device-wide counter, the
   // next claim issued before the current item is processed.  Claims below
@@ -427,7 +446,7 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
 
   // block tier: the overflowed tiles' roots as level 0 of a private queue
   const int nov = min(s.n_ovf, kOvfCap);
-  if (nov > 0) by_block = block_tier(a, s, nov, dev_roots);
+  if (nov > 0) by_block = block_tier<HT, CT, kNewton>(a, s, nov, dev_roots);
   trace_point(a.st, kTrLocal + 5);
   if (t == 0) {
     atomicAdd(covered, (int)(by_warps + by_block));
