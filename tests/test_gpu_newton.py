@@ -232,3 +232,28 @@ def test_grid2048_f64_n2_every_cell():
         assert _rel(got, want) <= REL64
         cur = got
     mdl.close()
+
+
+def test_newton_runs_in_the_private_tiers_and_matches_device_wide():
+    # the tiered step (mode 0) solves Newton in the warp tile forests; mode 1
+    # runs every cell on the device-wide levels; both give the oracle's result
+    lem = _lem()
+    h0 = synth.noise_surface(256, 256, 17)
+    par = dict(dx=100.0, K=0.05, m=0.5, U=1e-3, dt=1000.0)
+    p = oracle.params(**par)
+    want, _ = oracle.step_newton(h0, p, 1.5, 1e-12, 100)
+    got = {}
+    for mode in (0, 1):
+        h = torch.tensor(h0, device=_dev())
+        mdl = lem.Model(h, **par)
+        lem.lem_set_step_mode(mdl.ctx, mode)
+        mdl.set_slope_exponent(1.5, 1e-12, 100)
+        mdl.step(1)
+        mdl.sync()
+        got[mode] = h.cpu().numpy()
+        if mode == 0:
+            warp, block, device = lem.lem_tier_stats(mdl.ctx)
+            assert warp > 0 and warp + block + device == h0.size
+        mdl.close()
+    for mode in (0, 1):
+        assert _rel(got[mode], want) <= REL64
