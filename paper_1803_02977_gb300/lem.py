@@ -20,6 +20,32 @@ LEM_F64, LEM_F32 = 0, 1
 _lib = None
 
 
+class _nvtx:
+    """An NVTX range around a host call, so that a profiler's timeline names
+    each stage and step; a no-op where NVTX is unavailable (markers only: a
+    call never fails over them)."""
+
+    def __init__(self, name):
+        self.name = name
+        self.pushed = False
+
+    def __enter__(self):
+        try:
+            torch.cuda.nvtx.range_push(self.name)
+            self.pushed = True
+        except Exception:  # noqa: BLE001
+            pass
+        return self
+
+    def __exit__(self, *exc):
+        if self.pushed:
+            try:
+                torch.cuda.nvtx.range_pop()
+            except Exception:  # noqa: BLE001
+                pass
+        return False
+
+
 class LemError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -325,7 +351,8 @@ class Batch:
         lem_batch_set_config(self.b, block_threads, items_per_thread)
 
     def step(self, nsteps=1):
-        lem_batch_step(self.b, nsteps)
+        with _nvtx("lem.batch_step"):
+            lem_batch_step(self.b, nsteps)
 
     def sync(self):
         lem_batch_sync(self.b)
@@ -412,33 +439,39 @@ class Model:
 
     def receivers(self):
         rec = torch.empty(self.N, dtype=torch.int32, device=self.h.device)
-        lem_receivers(self.ctx, rec)
+        with _nvtx("lem.receivers"):
+            lem_receivers(self.ctx, rec)
         return rec
 
     def donors(self):
         dnum = torch.empty(self.N, dtype=torch.int32, device=self.h.device)
         donor = torch.empty(self.N * 8, dtype=torch.int32, device=self.h.device)
-        lem_donors(self.ctx, dnum, donor)
+        with _nvtx("lem.donors"):
+            lem_donors(self.ctx, dnum, donor)
         return dnum, donor.view(self.N, 8)
 
     def levels(self, want_depth=True):
         q = torch.empty(self.N, dtype=torch.int32, device=self.h.device)
         lev = torch.empty(self.N + 1, dtype=torch.int64, device=self.h.device)
         depth = torch.empty(self.N, dtype=torch.int32, device=self.h.device) if want_depth else None
-        L = lem_levels(self.ctx, q, lev, depth)
+        with _nvtx("lem.levels"):
+            L = lem_levels(self.ctx, q, lev, depth)
         return q, lev[:L + 1], depth
 
     def accumulate(self):
         dt = torch.int64 if self.count_bits == 64 else torch.int32
         cnt = torch.empty(self.N, dtype=dt, device=self.h.device)
-        lem_accumulate(self.ctx, cnt)
+        with _nvtx("lem.accumulate"):
+            lem_accumulate(self.ctx, cnt)
         return cnt
 
     def erode(self):
-        lem_erode(self.ctx)
+        with _nvtx("lem.erode"):
+            lem_erode(self.ctx)
 
     def step(self, nsteps=1):
-        lem_step(self.ctx, nsteps)
+        with _nvtx("lem.step"):
+            lem_step(self.ctx, nsteps)
 
     def set_receivers(self, rec):
         lem_set_receivers(self.ctx, rec)
@@ -447,13 +480,15 @@ class Model:
         lem_set_slope_exponent(self.ctx, n, eps, max_iter)
 
     def fill(self):
-        lem_fill(self.ctx)
+        with _nvtx("lem.fill"):
+            lem_fill(self.ctx)
 
     def accumulate_mfd(self, p=1.0, w=None):
         """(A, number of levels) of Eq. 2 with multiple flow directions."""
         A = torch.empty(self.ny, self.nx, dtype=torch.float64, device=self.h.device)
         wt = None if w is None else w.to(torch.float64).contiguous()
-        L = lem_accumulate_mfd(self.ctx, A, p, wt)
+        with _nvtx("lem.accumulate_mfd"):
+            L = lem_accumulate_mfd(self.ctx, A, p, wt)
         return A, L
 
     def set_fill(self, on):
