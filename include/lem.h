@@ -159,7 +159,9 @@ LEM_API int lem_accumulate(lem_ctx* ctx, void* dev_counts);
  *  nlevels    if not NULL, receives the number of levels
  * The D8 stages (receivers, levels, counts, erosion) are not affected.  The
  * first call allocates 16 bytes of scratch per cell.  Synchronises the
- * stream. */
+ * stream and returns the kernel's status.  LEM_EINVAL for a NULL context
+ * or dev_A or a p that is not finite and positive; LEM_ESTATE without bound
+ * elevations. */
 LEM_API int lem_accumulate_mfd(lem_ctx* ctx, double p, const double* dev_w, double* dev_A,
                                int64_t* nlevels);
 
@@ -219,9 +221,10 @@ LEM_API int lem_set_slope_exponent(lem_ctx* ctx, double n, double eps, int max_i
  * elevation type (double or float).  The result is unique and bit-exact;
  * elevations must be finite.  One cooperative launch, asynchronous on the
  * context's stream; the first call allocates a scratch of nx*ny elevations
- * and nx*ny int32 plus two bytes per 32 x 32 tile.  LEM_ETIMEOUT (reported by the next
- * synchronising call) if a device wait ran out.  Invalidates the derived
- * stages. */
+ * and nx*ny int32 plus two bytes per 32 x 32 tile.  LEM_EINVAL for a NULL
+ * context, LEM_ESTATE without bound elevations; LEM_ETIMEOUT (reported by
+ * the next synchronising call) if a device wait ran out.  Invalidates the
+ * derived stages. */
 LEM_API int lem_fill(lem_ctx* ctx);
 
 /* With on = 1, every later lem_step step begins with lem_fill (each step is
