@@ -36,31 +36,32 @@ def _free_port():
 
 
 def _tiny_batch():
-    sides = [7, 12, 9, 15, 5, 11, 8, 6]
-    return [synth.noise_surface(s, s + 1, 1000 + r) for r, s in enumerate(sides)]
+    return synth.batch_workload(count=9, side_lo=5, side_hi=17, seed=11)
+
+
+def _oracle_advance(surfaces, pars, steps):
+    # the oracle stands in for the GPU step on a CPU-only run
+    import oracle
+    return [oracle.run(s.astype(np.float64), oracle.params(**p), steps).astype(np.float32)
+            for s, p in zip(surfaces, pars)]
 
 
 def _worker(rank, world, port, out):
-    import torch
-    import oracle
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    surfaces = _tiny_batch()
-    parts = sharding.lpt_partition([s.size for s in surfaces], world)
-    mine = parts[rank]
-    p = oracle.params(K=2e-5)
-    sums = torch.zeros(len(surfaces), dtype=torch.float64)
-    for i in mine:
-        sums[i] = float(oracle.run(surfaces[i], p, 3).sum())
-    dist.all_reduce(sums)  # host-side gather of results: each slot written by one rank
+    bw = _tiny_batch()
+    parts = sharding.lpt_partition([s * s for s in bw.sides], world)
+    res = sharding.run_shard(None, bw, parts[rank], 3, advance=_oracle_advance)
+    full = sharding.gather_surfaces(res["surfaces"], bw.count, rank, world)
     if rank == 0:
-        out.put(sums.numpy().tolist())
+        out.put([np.asarray(s).tolist() for s in full])
+    else:
+        assert full is None
     dist.destroy_process_group()
 
 
 def test_two_rank_gloo_shards_match_single_process():
-    import oracle
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -71,6 +72,18 @@ def test_two_rank_gloo_shards_match_single_process():
     for pr in procs:
         pr.join(timeout=60)
         assert pr.exitcode == 0
-    p = oracle.params(K=2e-5)
-    want = [float(oracle.run(s, p, 3).sum()) for s in _tiny_batch()]
-    assert np.allclose(got, want, rtol=0, atol=0)
+    bw = _tiny_batch()
+    single = sharding.run_shard(None, bw, list(range(bw.count)), 3, advance=_oracle_advance)
+    want = sharding.gather_surfaces(single["surfaces"], bw.count, 0, 1)
+    assert len(got) == bw.count
+    for r in range(bw.count):
+        g = np.asarray(got[r], np.float32)
+        assert g.shape == want[r].shape
+        assert np.array_equal(g, want[r]), f"realization {r} differs"
+        # each realization really advanced
+        assert not np.array_equal(g, bw.initial(r).astype(np.float32))
+
+
+def test_gather_rejects_missing_or_duplicate_realizations():
+    with pytest.raises(KeyError):
+        sharding.gather_surfaces({0: 1, 2: 3}, 3, 0, 1)
