@@ -27,7 +27,12 @@ namespace {
 
 constexpr int kMaxCells = LEM_NOALLOC_MAX_CELLS;
 constexpr int kMaxBlocks = 256;       // blocks of the cooperative grid used at most
-constexpr int kPcap = 4096;           // private-queue entries per block
+// private-queue entries per block.  The context path sizes a block's share
+// as max(2*ceil(N/grid), 4096); for N <= LEM_NOALLOC_MAX_CELLS and the
+// 152-block grid of a GB300 that is 4096 as well (2*ceil(2^18/152) = 3450).
+// On a GPU with fewer SMs the share is smaller than the context path's, which
+// only sends more trees to the device-wide tier: the results are the same.
+constexpr int kPcap = 4096;
 constexpr int kMaxDevices = 64;
 
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -70,7 +75,7 @@ __global__ void noalloc_prepare_kernel(unsigned char* base, int N, double Kdt, d
   float* gtab = reinterpret_cast<float*>(base + kOffGtab);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     memset(st, 0, sizeof(DevState));
-    st->wait_limit_ns = 2000000000ull;
+    st->wait_limit_ns = 2000000000ull;  // fixed 2 s bound on every device-side wait
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kTableN; i += gridDim.x * blockDim.x) {
     const double A = __dmul_rn((double)i, area_scale);
@@ -107,6 +112,18 @@ extern "C" LEM_API int lem_step_noalloc(int nx, int ny, double* dev_h, double dx
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return status_of(e);
   if (dev < 0 || dev >= kMaxDevices) return LEM_EINVAL;
+  // the kernel runs on the current device: dev_h must be that device's memory
+  // (a pointer to another GPU's memory would be dereferenced across devices)
+  {
+    cudaPointerAttributes pa;
+    e = cudaPointerGetAttributes(&pa, dev_h);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return LEM_EINVAL;
+    }
+    if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != dev)
+      return LEM_EINVAL;
+  }
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_scratch);

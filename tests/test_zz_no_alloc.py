@@ -43,6 +43,31 @@ def test_noalloc_matches_context_step_on_two_calls():
 
 
 @pytest.mark.gpu
+def test_noalloc_reuses_its_array_across_sizes_and_parameters():
+    """A smaller grid after a larger one and back, with other parameters on
+    every call: stale codes, queues and counts beyond the smaller grid and
+    the erosion tables of the previous call must not leak into the next."""
+    from paper_1803_02977_gb300 import lem
+    dev = torch.device("cuda:0")
+    calls = [((257, 199), dict(dx=100.0, K=2e-5, m=0.45, U=1e-3, dt=1000.0), 78),
+             ((100, 60), dict(dx=50.0, K=4e-5, m=0.5, U=2e-3, dt=500.0), 79),
+             ((257, 199), dict(dx=120.0, K=1e-5, m=0.55, U=1e-3, dt=800.0), 80)]
+    for (nx, ny), par, seed in calls:
+        h0 = synth.noise_surface(nx, ny, seed, south_tilt=1e-4)
+        ref = torch.tensor(h0, device=dev)
+        mdl = lem.Model(ref, **par)
+        mdl.step(2)
+        mdl.sync()
+        mdl.close()
+        got = torch.tensor(h0, device=dev)
+        rc = lem.lem_step_noalloc(got, par["dx"], par["K"], par["m"], par["U"], par["dt"], 2)
+        assert rc == lem.LEM_OK, f"{nx}x{ny}: status {rc}"
+        want = ref.cpu().numpy()
+        err = np.abs(got.cpu().numpy() - want).max()
+        assert err <= REL64 * max(np.abs(want).max(), 1.0), f"{nx}x{ny}: max |dh| {err}"
+
+
+@pytest.mark.gpu
 def test_noalloc_rejects_oversized_grid_before_device_work():
     from paper_1803_02977_gb300 import lem
     dev = torch.device("cuda:0")
