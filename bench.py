@@ -3,12 +3,14 @@
 
 A step is one full time step of the method (receivers, donors, levels,
 accumulation, uplift + erosion) over the whole synthetic grid.  Default
-workload: 2048 x 2048 FP64 grid, seeded [0,1) noise plus a 1e-4 south tilt,
-dx = 100 m, K = 1e-5 /yr, m = 0.5, U = 1e-3 m/yr, dt = 1000 yr.
+workload: the paper's 10000 x 10000 size, FP32 elevations with FP64 slope
+tests and int64 cell counts, seeded [0,10) noise, dx = 100 m, K = 2e-5 /yr,
+m = 0.45, U = 1e-3 m/yr, dt = 500 yr; the timed window ends at the
+configuration's 100th step (earlier steps run untimed first).
 
-The working set of that grid (~72 MB) fits in the 129 MB L2, so every timed
-step is bracketed by CUDA events on the launching stream and the L2 is
-flushed (a 512 MiB write) between timed steps, outside the events.
+Its working set (~0.6 GB of elevations, codes and masks) is larger than the
+129 MB L2; the L2 is also flushed (a 512 MiB write) between timed steps,
+outside the CUDA events that bracket each step on the launching stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   # the CPU oracle on the host cores
@@ -16,7 +18,8 @@ flushed (a 512 MiB write) between timed steps, outside the events.
 
 Under torchrun each rank advances its own replica of the grid (one grid does
 not shard: its level order is global); the reported value is the sum over
-ranks divided by the slowest rank's time.
+ranks divided by the slowest rank's time.  The batch of realizations (a form
+measured beside the main line) shards by LPT over the ranks.
 """
 from __future__ import annotations
 
@@ -53,17 +56,18 @@ def algo_bytes(P, Ab):
 def parse():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", default="grid2048_f64")
+    ap.add_argument("--workload", default="grid10000_f32")
     ap.add_argument("--flush-mib", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-phases", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32, 10000^2, batch and adjoint measurements")
-    ap.add_argument("--batch-steps", type=int, default=10)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+    ap.add_argument("--batch-steps", type=int, default=200,
+                    help="steps of every realization of the 512-grid batch")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--sweep", action="store_true",
                     help="time the FP64 step at edge lengths 100 .. 16000 and fit the\n"
@@ -166,7 +170,33 @@ def cpu_oracle_rate(w, target_s, h0=None):
     cells = h0.size
     return {"value": cells * nsteps / el, "unit": METRIC, "cores": 1, "kind": "oracle",
             "sample": f"{nsteps} oracle steps on a {h0.shape[1]}x{h0.shape[0]} grid of the "
-                      f"same recipe, {el:.1f} s, single-threaded C (-O2, FP64)"}
+                      f"same recipe, {el:.1f} s, single-threaded C (-O2, FP64); the metric "
+                      f"is per cell-step, so the configuration's step count does not change it",
+            "host": host_info()}
+
+
+def host_info():
+    """The host's logical CPU count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
 
 
 def run_reference(args):
@@ -202,7 +232,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(w, args),
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_info()},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -229,13 +259,11 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = synth.workload(args.workload)
-    tdtype = torch.float64 if w.dtype == "f64" else torch.float32
     P = 8 if w.dtype == "f64" else 4
     Ab = 8 if w.area_dtype == "i64" else 4
-    count_bits = 8 * Ab
     h0_np = w.initial().astype(np.float64 if P == 8 else np.float32)
     N = w.nx * w.ny
-    par = dict(dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt, count_bits=count_bits)
+    par = dict(dx=w.dx, K=w.K, m=w.m, U=w.U, dt=w.dt, count_bits=8 * Ab)
 
     h = torch.tensor(h0_np, device=dev)
     mdl = lem.Model(h, **par)
@@ -246,12 +274,18 @@ def run_ours(args):
         if ws > 1:
             dist.barrier()
 
+    # the timed window ends at the configuration's last step: the steps
+    # before the warm-up run untimed, in one launch
+    K = args.steps
+    ahead = max(0, w.steps - K - args.warmup)
+    if ahead:
+        mdl.step(ahead)
     for _ in range(args.warmup):
         mdl.step(1)
         flush.zero_()
     mdl.sync()
+    tiers0 = lem.lem_tier_stats(mdl.ctx)
 
-    K = args.steps
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     barrier()
@@ -278,19 +312,28 @@ def run_ours(args):
     value = N * K * ws / (tot_ms / 1e3)
     ms_per_step = tot_ms / K
 
-    # which tier handled the cells (warp tiles, block queues, device-wide)
-    tiers = lem.lem_tier_stats(mdl.ctx)
+    # which tier handled the cells of the timed steps (warp tiles, block
+    # queues, device-wide levels)
+    tiers = [b_ - a_ for a_, b_ in zip(tiers0, lem.lem_tier_stats(mdl.ctx))]
     tier_frac = [x / max(1, sum(tiers)) for x in tiers]
 
-    # one traced step after the timed region: in-kernel time per phase
-    timeline = traced_step(lem, mdl, flush)
-
-    # level count of the state reached (outside the timed region)
+    # level count of the state the timed window ended on (outside the timed
+    # region; the stage calls recompute the graph of the current surface)
     mdl.receivers()
     L = lem.lem_levels(mdl.ctx)
 
-    # per-phase split through the stage-by-stage calls (outside the timed region)
-    phases = None
+    # one traced launch after the timed region: in-kernel time per phase of
+    # the production step, and the achieved bandwidth of each phase
+    ab = algo_bytes(P, Ab)
+    peak = measured_peaks().get("hbm_gbs")
+    tc0 = lem.lem_tier_stats(mdl.ctx)
+    timeline = traced_step(lem, mdl, flush)
+    tcells = [b_ - a_ for a_, b_ in zip(tc0, lem.lem_tier_stats(mdl.ctx))]
+    phases = step_phase_split(timeline, tcells, ab, N, peak)
+
+    # per-stage split through the stage-by-stage calls (device-wide levels),
+    # on the initial surface (outside the timed region)
+    stage_calls = None
     if not args.no_phases:
         hp = torch.tensor(h0_np, device=dev)
         mp = lem.Model(hp, **par)
@@ -312,117 +355,57 @@ def run_ours(args):
             if r > 0:
                 for i, k in enumerate(PHASES):
                     acc[k] += evs[i].elapsed_time(evs[i + 1]) / reps
-        ab = algo_bytes(P, Ab)
-        peak = measured_peaks().get("hbm_gbs")
-        phases = {k: {"ms": acc[k], "algo_bytes_per_cell": ab[k],
-                      "gbs": ab[k] * N / (acc[k] / 1e3) / 1e9,
-                      "cell_steps_per_s": N / (acc[k] / 1e3)} for k in PHASES}
+            hp.copy_(torch.tensor(h0_np, device=dev))
+        stage_calls = {k: {"ms": acc[k], "algo_bytes_per_cell": ab[k],
+                           "gbs": ab[k] * N / (acc[k] / 1e3) / 1e9,
+                           "cell_steps_per_s": N / (acc[k] / 1e3)} for k in PHASES}
         if peak:
             for k in PHASES:
-                phases[k]["frac_of_measured_hbm"] = phases[k]["gbs"] / peak
+                stage_calls[k]["frac_of_measured_hbm"] = stage_calls[k]["gbs"] / peak
         mp.close()
+        del hp
 
-    # end to end through the public API: pinned host h -> device, one step,
-    # device -> pinned host, every step
-    hh = torch.tensor(h0_np).pin_memory()
-    hd = torch.empty_like(hh, device=dev)
-    me = lem.Model(hd, **par)
-    Ke = max(3, min(K, 20))
-    for _ in range(2):
-        hd.copy_(hh, non_blocking=True)
-        me.step(1)
-        hh.copy_(hd, non_blocking=True)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(Ke):
-        hd.copy_(hh, non_blocking=True)
-        me.step(1)
-        hh.copy_(hd, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    me.sync()
-    e2e_ms = e0.elapsed_time(e1)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = N * Ke * ws / (float(te.item()) / 1e3)
-    me.close()
+    e2e = measure_e2e(lem, h0_np, par, dev, max(3, min(K, 20)), ws)
+    mdl.close()
+    del h
+    torch.cuda.empty_cache()
 
     forms = None
     if not args.no_forms:
-        forms = {}
-        plain = N / (ms_per_step / 1e3)
-        if args.workload == "grid2048_f64":
-            ms32 = time_grid(lem, synth.workload("grid2048_f32"), min(K, 30), 3, flush, dev)
-            v32 = N / (float(np.mean(ms32)) / 1e3)
-            forms["fp32_same_grid"] = {"workload": "grid2048_f32", "ms_per_step": float(np.mean(ms32)),
-                                       "value": v32, "vs_plain_fp64": v32 / plain}
-            forms["fill"] = measure_fill(lem, w, flush, dev, plain)
-            forms["mfd_accumulation"] = measure_mfd(lem, w, flush, dev)
-            # Alg 6 with n-hat = 2 and 1.5 (Newton-Raphson in every tier)
-            for nh in (2.0, 1.5):
-                msn = time_grid(lem, w, min(K, 20), 3, flush, dev, slope_exponent=nh)
-                vn = N / (float(np.mean(msn)) / 1e3)
-                forms[f"slope_exponent_n{nh:g}"] = {
-                    "workload": w.name, "n_hat": nh, "eps_m": 1e-12, "max_iter": 100,
-                    "ms_per_step": float(np.mean(msn)), "value": vn, "vs_plain_fp64": vn / plain}
-        w10 = synth.workload("grid10000_f32")
-        ms10 = time_grid(lem, w10, 5, 2, flush, dev)
-        a10 = sum(algo_bytes(4, 8).values()) * w10.cells / (float(np.mean(ms10)) / 1e3) / 1e9
-        forms["grid10000_f32"] = {"ms_per_step": float(np.mean(ms10)),
-                                  "value": w10.cells / (float(np.mean(ms10)) / 1e3),
-                                  "achieved_gbs": a10,
-                                  "frac_of_measured_hbm": a10 / measured_peaks()["hbm_gbs"],
-                                  "paper_rb_gpu_p100_cell_steps_per_s": 1e8 * 120 / 70.0}
-        del flush
-        torch.cuda.empty_cache()
-        bt = measure_batch(lem, args.batch_steps, ws, rank, dev)
-        t = torch.tensor([bt["ms"], bt["plain_fp64_sample"]["ms"]], dtype=torch.float64,
-                         device=dev)
-        cs = torch.tensor([bt["cell_steps"], bt["plain_fp64_sample"]["cells"] * bt["steps"]],
-                          dtype=torch.float64, device=dev)
-        if ws > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dist.all_reduce(cs)
-        bt["value"] = float(cs[0]) / (float(t[0]) / 1e3)
-        bt["plain_fp64_sample"]["value"] = float(cs[1]) / (float(t[1]) / 1e3)
-        bt["vs_plain_fp64"] = bt["value"] / bt["plain_fp64_sample"]["value"]
-        bt["ranks"] = ws
-        forms["batch512_f32"] = bt
-        if rank == 0:
-            forms["adjoint_grid1024_f64"] = measure_adjoint(lem, dev)
+        forms = measure_forms(lem, synth, args, w, ms_per_step, flush, dev, ws, rank)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(w, args.cpu_seconds)
 
-    peaks = measured_peaks()
-    ab = algo_bytes(P, Ab)
     per_cell = sum(ab.values())
     achieved = per_cell * N / (ms_per_step / 1e3) / 1e9
-    peak = peaks.get("hbm_gbs")
     traffic, traffic_src = profiled_traffic(w.name)
+    kname = {("f64", 4): "<double, int, false>", ("f64", 8): "<double, long long, false>",
+             ("f32", 4): "<float, int, false>", ("f32", 8): "<float, long long, false>"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if peak else None, "traffic": traffic,
                 "traffic_source": traffic_src,
-                "kernel": "lem_step_kernel (one cooperative launch per step)",
+                "kernel": "lem::lem_step_kernel" + kname[(w.dtype, Ab)]
+                          + " (one cooperative launch per step)",
                 "algo_bytes_per_cell_step": per_cell,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peak else None}
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured"
+                               if peak else None}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
-            "config": config_of(w, args), "levels_after": int(L),
+            "config": config_of(w, args),
+            "window": {"first_timed_step": ahead + args.warmup + 1,
+                       "last_timed_step": ahead + args.warmup + K, "config_steps": w.steps},
+            "levels_after": int(L),
             "step_ms_min_median_max": [min(step_ms), float(np.median(step_ms)), max(step_ms)],
             "wall_s_timed_region": t_wall,
-            "roofline": roofline, "phases": phases, "timeline": timeline,
+            "roofline": roofline, "phases": phases, "stage_calls": stage_calls,
+            "timeline": timeline,
             "tier_cell_fraction": {"warp_tiles": tier_frac[0], "block_queues": tier_frac[1],
                                    "device_wide": tier_frac[2]},
-            "clocks": clk,
-            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": N * P,
-                    "d2h_bytes_per_step": N * P, "steps": Ke},
+            "clocks": clk, "e2e": e2e,
             "gpu_launches": K, "cpu_baseline": cpu, "forms": forms}
-    mdl.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -430,11 +413,166 @@ def run_ours(args):
     return 0
 
 
-def time_grid(lem, w, steps, warmup, flush, dev, slope_exponent=None, mode=None):
-    """Per-step device times (ms) of `steps` single-step lem_step calls on
-    workload w, L2 flushed between steps.  slope_exponent: Alg 6's Newton
-    form with that n-hat (eps 1e-12 m, at most 100 updates); mode: the
-    lem_set_step_mode form."""
+def step_phase_split(timeline, tier_cells, ab, N, peak):
+    """Achieved bandwidth of each phase of the production step from the
+    device trace (block 0's view of the traced launch's steady-state step):
+    the codes pass (Algs 1-2, P+2 bytes per cell) up to the grid barrier
+    after it, the warp and block tiers (Algs 3-6, the levels + accumulation +
+    erosion bytes of each cell they handled) up to the next barrier, and the
+    device-wide tier (the same bytes per cell it handled)."""
+    if not timeline:
+        return None
+    us = (timeline.get("steady_state_step") or timeline)["us"]
+    tot = max(1, sum(tier_cells))
+    nsteps = timeline.get("steps_in_launch", 1)
+    per = {k: v / nsteps for k, v in zip(("warp", "block", "device"), tier_cells)}
+    sweep = ab["levels"] + ab["accumulate"] + ab["erode"]
+    out = {}
+    parts = {"codes": (us["codes"] + us["codes_wait"], ab["receivers"] * N),
+             "tiles": (us["tiles_warp"] + us["tiles_block"] + us["tiles_wait"],
+                       sweep * (per["warp"] + per["block"])),
+             "device": (us["device_tier"], sweep * per["device"])}
+    for k, (t_us, nbytes) in parts.items():
+        if t_us <= 0 or nbytes <= 0:
+            out[k] = {"us": t_us, "algo_bytes": nbytes, "gbs": None, "frac_of_measured_hbm": None}
+            continue
+        gbs = nbytes / (t_us / 1e6) / 1e9
+        out[k] = {"us": t_us, "algo_bytes": nbytes, "gbs": gbs,
+                  "frac_of_measured_hbm": gbs / peak if peak else None}
+    out["codes"]["algo_bytes_per_cell"] = ab["receivers"]
+    out["tiles"]["algo_bytes_per_cell"] = sweep
+    out["tier_cells_per_step"] = {k: v for k, v in per.items()}
+    out["cells"] = N
+    out["source"] = "in-kernel %globaltimer trace, block 0, steady-state step of a 3-step launch"
+    del tot
+    return out
+
+
+def measure_e2e(lem, h0_np, par, dev, steps, ws):
+    """End to end through the public API with host buffers: every step the
+    elevations are copied from pinned host memory to the device, advanced one
+    step by lem_step, and copied back to pinned host memory.  Copies and the
+    step run on three streams over two device buffers, so the upload of step
+    i+1 and the download of step i-1 overlap step i (the context is bound to
+    step i's buffer before its launch); the timed region spans the first
+    upload to the last download."""
+    import torch
+    import torch.distributed as dist
+    hin = torch.from_numpy(np.ascontiguousarray(h0_np)).pin_memory()
+    hout = [torch.empty_like(hin).pin_memory() for _ in range(2)]
+    d = [torch.empty(hin.shape, dtype=hin.dtype, device=dev) for _ in range(2)]
+    me = lem.Model(d[0], **par)
+    comp = torch.cuda.current_stream()
+    s_up, s_down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    up_done = [torch.cuda.Event() for _ in range(2)]
+    comp_done = [torch.cuda.Event() for _ in range(2)]
+    down_done = [torch.cuda.Event() for _ in range(2)]
+
+    def one(i):
+        b = i & 1
+        if i >= 2:
+            s_up.wait_event(down_done[b])  # buffer b's previous result has left
+        with torch.cuda.stream(s_up):
+            d[b].copy_(hin, non_blocking=True)
+            up_done[b].record(s_up)
+        comp.wait_event(up_done[b])
+        lem.lem_bind_elevation(me.ctx, d[b], me.dtype)
+        me.step(1)
+        comp_done[b].record(comp)
+        s_down.wait_event(comp_done[b])
+        with torch.cuda.stream(s_down):
+            hout[b].copy_(d[b], non_blocking=True)
+            down_done[b].record(s_down)
+
+    for i in range(4):
+        one(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(comp)
+    s_up.wait_event(e0)
+    for i in range(steps):
+        one(i)
+    comp.wait_event(down_done[(steps - 1) & 1])
+    comp.wait_event(down_done[steps & 1])
+    e1.record(comp)
+    torch.cuda.synchronize()
+    me.sync()
+    ms = e0.elapsed_time(e1)
+    # the result of the last step, checked to have left the device intact
+    ok = bool(torch.equal(hout[(steps - 1) & 1], d[(steps - 1) & 1].cpu()))
+    me.close()
+    te = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    n = hin.numel()
+    nb = n * hin.element_size()
+    return {"value": n * steps * ws / (float(te.item()) / 1e3), "unit": METRIC,
+            "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": steps,
+            "ms_per_step": float(te.item()) / steps, "result_copied_back": ok,
+            "how": "pinned host -> device, lem_step, device -> pinned host every step; "
+                   "three streams, two device buffers (upload i+1 and download i-1 "
+                   "overlap step i)"}
+
+
+def measure_forms(lem, synth, args, w, ms_per_step, flush, dev, ws, rank):
+    """The other configurations and forms, each at its stated horizon."""
+    import torch
+    import torch.distributed as dist
+    forms = {}
+    N = w.nx * w.ny
+    plain_here = N / (ms_per_step / 1e3)
+    # the same grid in FP64 (the plain path the FP32 form must beat)
+    if w.name == "grid10000_f32":
+        w64 = synth.workload("grid10000_f64")
+        r = time_grid(lem, w64, 10, 3, flush, dev, horizon=w64.steps)
+        forms["grid10000_f64_same_grid"] = dict(r, workload=w64.name,
+                                                vs_fp32=r["value"] / plain_here)
+    # the 2048^2 workload, FP64 and FP32, timed on steps 481-500 of its 500
+    w2 = synth.workload("grid2048_f64")
+    r64 = time_grid(lem, w2, 20, 3, flush, dev, horizon=w2.steps)
+    forms["grid2048_f64"] = dict(r64, workload=w2.name)
+    w2f = synth.workload("grid2048_f32")
+    r32 = time_grid(lem, w2f, 20, 3, flush, dev, horizon=w2f.steps)
+    forms["grid2048_f32"] = dict(r32, workload=w2f.name, vs_plain_fp64=r32["value"] / r64["value"])
+    plain = r64["value"]
+    forms["fill"] = measure_fill(lem, w2, flush, dev, plain)
+    forms["mfd_accumulation"] = measure_mfd(lem, w2, flush, dev)
+    # Alg 6 with n-hat = 2 and 1.5 (Newton-Raphson in every tier)
+    for nh in (2.0, 1.5):
+        rn = time_grid(lem, w2, 20, 3, flush, dev, slope_exponent=nh)
+        forms[f"slope_exponent_n{nh:g}"] = dict(rn, workload=w2.name, n_hat=nh, eps_m=1e-12,
+                                                 max_iter=100, vs_plain_fp64=rn["value"] / plain)
+    del flush
+    torch.cuda.empty_cache()
+    bt = measure_batch(lem, args.batch_steps, ws, rank, dev)
+    t = torch.tensor([bt["ms"], bt["plain_fp64"]["ms"]], dtype=torch.float64, device=dev)
+    cs = torch.tensor([bt["cell_steps"], bt["plain_fp64"]["cells"] * bt["steps"]],
+                      dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(cs)
+    bt["value"] = float(cs[0]) / (float(t[0]) / 1e3)
+    bt["plain_fp64"]["value"] = float(cs[1]) / (float(t[1]) / 1e3)
+    bt["vs_plain_fp64"] = bt["value"] / bt["plain_fp64"]["value"]
+    peak = measured_peaks().get("hbm_gbs")
+    per_cell = sum(algo_bytes(4, 4).values())
+    bt["algo_bytes_per_cell_step"] = per_cell
+    bt["achieved_gbs"] = per_cell * bt["value"] / 1e9
+    bt["frac_of_measured_hbm"] = bt["achieved_gbs"] / peak if peak else None
+    bt["ranks"] = ws
+    forms["batch512_f32"] = bt
+    if rank == 0:
+        forms["adjoint_grid1024_f64"] = measure_adjoint(lem, dev)
+    return forms
+
+
+def time_grid(lem, w, steps, warmup, flush, dev, slope_exponent=None, mode=None, horizon=None):
+    """`steps` single-step lem_step calls on workload w, each bracketed by
+    CUDA events, L2 flushed between them; with `horizon`, the timed window
+    ends at that step (the steps before it run untimed).  slope_exponent:
+    Alg 6's Newton form with that n-hat (eps 1e-12 m, at most 100 updates);
+    mode: the lem_set_step_mode form.  Returns the mean time per step, the
+    rate, the window, the level count of the state reached and the tiers."""
     import torch
     P = 8 if w.dtype == "f64" else 4
     count_bits = 64 if w.area_dtype == "i64" else 32
@@ -445,11 +583,16 @@ def time_grid(lem, w, steps, warmup, flush, dev, slope_exponent=None, mode=None)
     if mode is not None:
         lem.lem_set_step_mode(mdl.ctx, mode)
     stream = torch.cuda.current_stream()
+    ahead = max(0, (horizon or 0) - steps - warmup)
+    if ahead:
+        mdl.step(ahead)
     for _ in range(warmup):
         mdl.step(1)
         flush.zero_()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
+    mdl.sync()
+    t0 = lem.lem_tier_stats(mdl.ctx)
     torch.cuda.synchronize()
     for e0, e1 in ev:
         e0.record(stream)
@@ -459,8 +602,14 @@ def time_grid(lem, w, steps, warmup, flush, dev, slope_exponent=None, mode=None)
     torch.cuda.synchronize()
     mdl.sync()
     ms = [a.elapsed_time(b) for a, b in ev]
+    tiers = [b_ - a_ for a_, b_ in zip(t0, lem.lem_tier_stats(mdl.ctx))]
+    mdl.receivers()
+    L = lem.lem_levels(mdl.ctx)
     mdl.close()
-    return ms
+    mean = float(np.mean(ms))
+    return {"ms_per_step": mean, "value": w.cells / (mean / 1e3), "steps_timed": steps,
+            "window": [ahead + warmup + 1, ahead + warmup + steps], "levels_after": int(L),
+            "tier_cell_fraction": [x / max(1, sum(tiers)) for x in tiers]}
 
 
 def measure_fill(lem, w, flush, dev, plain, reps=5):
@@ -559,36 +708,22 @@ def measure_mfd(lem, w, flush, dev, reps=5, p=1.1):
     return out
 
 
-def measure_batch(lem, steps, ws, rank, dev, count=512, sample_every=8):
+def measure_batch(lem, steps, ws, rank, dev, count=512):
     """The 512-realization FP32 batch in one launch (autotuned shape), this
-    rank's LPT shard, against the plain FP64 path run one grid at a time on
-    every sample_every-th realization of the shard."""
+    rank's LPT shard, `steps` steps of every realization; against the plain
+    FP64 path run one grid at a time on every realization of the shard, for
+    the same steps (the same total cell-steps)."""
     import torch
     from paper_1803_02977_gb300 import autotune, sharding, synth
     bw = synth.batch_workload(count=count)
     sizes = [s * s for s in bw.sides]
     mine = sharding.lpt_partition(sizes, ws)[rank]
-    surfaces = [bw.initial(r) for r in mine]
-    B = lem.Batch(surfaces, dx=bw.dx, K=[bw.K[r] for r in mine], m=[bw.m[r] for r in mine],
-                  U=bw.U, dt=bw.dt)
-    shape, tune_ms = autotune.tune_batch(B, steps=1)
-    B.step(1)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    B.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    B.sync()
-    ms = e0.elapsed_time(e1)
+    out = sharding.run_shard(lem, bw, mine, steps, tune=True)
     cells = sum(sizes[r] for r in mine)
-    B.close()
-    del B
-    # plain FP64 path, one grid at a time, on a sample of the shard
-    sample = mine[::sample_every]
-    plain_ms, plain_cells = 0.0, 0
-    for r in sample:
+    # plain FP64 path, one grid at a time, every realization of the shard
+    stream = torch.cuda.current_stream()
+    plain_ms = 0.0
+    for r in mine:
         h = torch.tensor(bw.initial(r), device=dev)
         mdl = lem.Model(h, dx=bw.dx, K=bw.K[r], m=bw.m[r], U=bw.U, dt=bw.dt)
         mdl.step(1)
@@ -599,14 +734,14 @@ def measure_batch(lem, steps, ws, rank, dev, count=512, sample_every=8):
         b.record(stream)
         torch.cuda.synchronize()
         plain_ms += a.elapsed_time(b)
-        plain_cells += sizes[r]
         mdl.close()
-    return {"ms": ms, "cells": cells, "cell_steps": cells * steps, "realizations": len(mine),
-            "steps": steps, "shape": list(shape),
-            "autotune_ms_per_step": {k: round(v, 3) for k, v in tune_ms.items()},
-            "plain_fp64_sample": {"realizations": len(sample), "cells": plain_cells,
-                                  "ms": plain_ms,
-                                  "value": plain_cells * steps / (plain_ms / 1e3)}}
+    return {"ms": out["ms"], "cells": cells, "cell_steps": cells * steps,
+            "realizations": len(mine), "steps": steps, "shape": list(out["shape"]),
+            "autotune_ms_per_step": {k: round(v, 3) for k, v in out["tune_ms"].items()},
+            "plain_fp64": {"realizations": len(mine), "cells": cells, "ms": plain_ms,
+                           "value": cells * steps / (plain_ms / 1e3),
+                           "how": "one lem_step launch of all steps per realization, "
+                                  "one realization after another"}}
 
 
 def measure_adjoint(lem, dev, nsteps=50, ckpt=10):
