@@ -805,6 +805,8 @@ def traced_step(lem, mdl, flush, nsteps=3):
                 key = "codes_wait"
             elif ph == "tiles_end":
                 key = "tiles_wait"
+            elif ph == "block_end":
+                key = "tiles_block"
             else:
                 key = "device_tier"
             out[key] += us

@@ -23,7 +23,12 @@
  *    which synchronise that stream.
  *  - Every call returns a status (LEM_OK or a negative LEM_E* code) and
  *    never throws.  Errors found by a kernel (a receiver cycle, a timed-out
- *    device wait) are sticky and reported by the next synchronising call.
+ *    device wait, a non-finite elevation) are sticky and reported by the
+ *    next synchronising call.
+ *  - Elevations must be finite.  Alg 1 checks every value it reads while
+ *    computing the receivers of interior cells: a NaN or infinity is
+ *    reported as LEM_EINVAL, and lem_step then stops before it changes any
+ *    elevation of that step (lem_receivers still writes its outputs).
  *  - A context is not thread-safe; use one per host thread.
  */
 #ifndef LEM_H
@@ -52,7 +57,9 @@ enum {
   LEM_ECUDA = -3,     /* a CUDA runtime call failed                            */
   LEM_ETIMEOUT = -4,  /* a bounded device-side wait ran out                    */
   LEM_ESTATE = -5,    /* a stage was called before its inputs were computed    */
-  LEM_EOVERFLOW = -6  /* grid too large for 32-bit cell addresses              */
+  LEM_EOVERFLOW = -6, /* grid too large for 32-bit cell addresses              */
+  LEM_EBOUNDS = -7    /* an index check of the LEM_DEBUG build failed (the      */
+                      /* access was skipped; liblem_debug.so only)              */
 };
 
 /* Elevation element types. */
@@ -244,6 +251,31 @@ LEM_API int lem_fill_stats(lem_ctx* ctx, int64_t* stats);
  * device; reported by the next synchronising call). */
 LEM_API int lem_set_receivers(lem_ctx* ctx, const int32_t* dev_rec);
 
+/* The receiver graph (Alg 1) and donor masks (Alg 2) that the last
+ * lem_step step -- or the last lem_receivers call, whichever ran later --
+ * computed from its input elevations.  dev_rec (nx*ny int32, self = NoFlow)
+ * and dev_mask (nx*ny bytes, bit k set iff neighbour k drains into the cell,
+ * k in the neighbour order above) may each be NULL.  Asynchronous;
+ * LEM_ESTATE if no step or receivers call has run yet. */
+LEM_API int lem_last_graph(lem_ctx* ctx, int32_t* dev_rec, uint8_t* dev_mask);
+
+/* Checkpoint / resume.  A state is a byte blob of *bytes = 32 + nx*ny *
+ * (8 or 4) bytes (lem_state_size): a header (format tag, grid size,
+ * element type, the number of lem_step steps taken, and whether the device
+ * tier's next deep step starts by pointer jumping) followed by the bound
+ * elevations.  lem_get_state writes it to buf, lem_set_state copies it back
+ * into the bound elevations and restores the step count and the hint, so
+ * that the steps after a resume equal, bit for bit, those the saved context
+ * would have taken.  buf may be host or device memory (the copies use
+ * unified addressing); both calls synchronise the context's stream.
+ * LEM_EINVAL for a NULL pointer, a buffer smaller than the state, or (set)
+ * a header of another grid or element type; LEM_ESTATE without bound
+ * elevations.  The receiver graph, parameters, uplift field and step mode
+ * are not part of the state. */
+LEM_API int lem_state_size(lem_ctx* ctx, int64_t* bytes);
+LEM_API int lem_get_state(lem_ctx* ctx, void* buf, int64_t bytes);
+LEM_API int lem_set_state(lem_ctx* ctx, const void* buf, int64_t bytes);
+
 /* Synchronise the context's stream and return the sticky device status
  * (then cleared). */
 LEM_API int lem_sync(lem_ctx* ctx);
@@ -271,6 +303,21 @@ LEM_API int lem_selftest_wait(lem_ctx* ctx);
  * the same elevations; the integer stages are identical. */
 LEM_API int lem_set_step_mode(lem_ctx* ctx, int mode);
 
+/* Work decomposition of lem_step (mode 0), for the package's autotuner.
+ *  band_chunks  FP32 elevations: the codes pass (Algs 1-2) takes work items
+ *               of 30 columns x (8*band_chunks - 4) rows, staged in chunks of
+ *               8 rows; 2 .. 16, or 0 for the default (the largest that
+ *               leaves four items per warp).  FP64 elevations ignore it.
+ *  half_tiles   1: the warp tier claims every 32-column tile as two
+ *               half-height items (8 -> 4 rows with FP64 elevations, 12 -> 6
+ *               with FP32); 0 (the default): only the last tiles of a step.
+ * Receivers and masks do not depend on either; elevations do not either
+ * while no tree needs the device tier's pointer-jumping form (whose sums
+ * associate differently, within a few units in the last place).
+ * LEM_EINVAL for other values.  lem_get_tiling returns the values in use. */
+LEM_API int lem_set_tiling(lem_ctx* ctx, int band_chunks, int half_tiles);
+LEM_API int lem_get_tiling(lem_ctx* ctx, int* band_chunks, int* half_tiles);
+
 /* Number of lem_step steps completed without and with device-wide levels
  * since the context was created (synchronises). */
 LEM_API int lem_step_stats(lem_ctx* ctx, int64_t* private_steps, int64_t* device_wide_steps);
@@ -279,6 +326,20 @@ LEM_API int lem_step_stats(lem_ctx* ctx, int64_t* private_steps, int64_t* device
  * tier: cells[0] warp tiles in shared memory, cells[1] block-private queues,
  * cells[2] device-wide levels (synchronises).  cells must hold 3 entries. */
 LEM_API int lem_tier_stats(lem_ctx* ctx, int64_t* cells);
+
+/* The device-wide tier's pointer-jumping form (mode 0, n-hat = 1): trees
+ * deeper than the device tier's level limit (max(64, nx*ny/2^15)
+ * breadth-first levels) are counted by ranking their Euler tours and eroded
+ * by composing each cell's affine update along its receivers, in O(log
+ * depth) device-wide rounds instead of one per level; once a step needed
+ * it, the next step's deep trees go to it directly (and block-private
+ * queues hold at most 256 levels).  Counts are exact; elevations are within
+ * a few units in the last place of the level-by-level sweep (FP64
+ * accumulation for either elevation type).  stats[0]: steps that used it
+ * since the context was created; stats[1]: erosion rounds of the latest
+ * (synchronises).  The first lem_step in mode 0 allocates its scratch, 44
+ * bytes per cell (grids below 2^30 cells). */
+LEM_API int lem_jump_stats(lem_ctx* ctx, int64_t* stats);
 
 /* Device-side tracing of the step kernel's timeline: with capacity > 0,
  * later launches record, after every device-wide barrier, the GPU global
@@ -291,7 +352,10 @@ LEM_API int lem_trace_enable(lem_ctx* ctx, int capacity);
  * recorded since the last read (entries beyond the capacity are dropped).
  * Tags: 1 start, 2 receivers, 3 level 0, 4 wide level, 5 narrow levels,
  * 6 wide accumulation, 7 narrow accumulation, 8 uplift, 9 wide erosion,
- * 10 narrow erosion. */
+ * 10 narrow erosion, 11-13 block-private levels, accumulation, erosion,
+ * 14 step end, 15 block 0 reached a barrier, 16 warp and block tiers done,
+ * 17 jumping tier: tour built, 18 one ranking round, 19 counts and factors,
+ * 20 one erosion-jumping round, 21 block tier done on every block. */
 LEM_API int lem_trace_read(lem_ctx* ctx, int64_t* ns, int32_t* tags, int cap, int* n);
 
 /* Reverse-mode gradient of nsteps time steps (Alg 5 + Alg 6, n-hat = 1)
@@ -381,7 +445,10 @@ LEM_API int lem_batch_sync(lem_batch* batch);
  * in the library's device image, held by every GPU that loads the library
  * until the process exits.
  *  - Grids with nx*ny > LEM_NOALLOC_MAX_CELLS (or nx, ny < 3, or invalid
- *    parameters) are rejected with LEM_EINVAL before any device work.
+ *    parameters) are rejected with LEM_EINVAL before any device work, and so
+ *    is a dev_h that is not memory of the current device.
+ *  - Every device-side wait (grid barriers) is bounded by a fixed 2 s; a
+ *    wait that runs out makes the call return LEM_ETIMEOUT.
  *  - The first call on each device looks up the array's device address with
  *    that device current; make that first call before any stream capture.
  *  - Every call on a device shares the one array and leaves its contents

@@ -1,11 +1,14 @@
-"""Autotuner for the batched form's kernel shape.
+"""Autotuner for the kernels' work decomposition.
 
-Times every supported (threads per block, entries per thread) shape on a
-copy of the batch's own elevations for a few steps, keeps the fastest, and
-caches the choice in a JSON file keyed by GPU name and the batch's size
-profile (number of realizations and a log2 histogram of their cell counts),
-so later batches of the same profile skip the timing.  All shapes compute
-identical results; only speed differs.
+tune_batch times every supported (threads per block, entries per thread)
+shape of the batched form on a copy of the batch's own elevations; tune_step
+times the single-grid step's tilings (lem_set_tiling: rows per work item of
+the FP32 codes pass, whole or half-height warp tiles).  Each keeps the
+fastest and caches the choice in a JSON file keyed by GPU name and the
+problem (the batch's size profile -- number of realizations and a log2
+histogram of their cell counts -- or the grid's size and types), so later
+runs of the same problem skip the timing.  All choices compute identical
+results; only speed differs.
 """
 from __future__ import annotations
 
@@ -86,3 +89,56 @@ def tune_batch(batch: "lem.Batch", steps: int = 2, use_cache: bool = True):
         cache[key] = {"shape": [bd, pi], "ms": timings}
         _store(cache)
     return (bd, pi), timings
+
+
+# ---- the single-grid step (lem_set_tiling) ------------------------------------
+
+STEP_BAND_CHUNKS = (2, 4, 6, 8, 11, 14, 16)
+
+
+def step_key(model: "lem.Model") -> str:
+    name = torch.cuda.get_device_name(model.h.device)
+    dt = "f64" if model.dtype == lem.LEM_F64 else "f32"
+    return f"{name}|step|{dt}|c{model.count_bits}|{model.nx}x{model.ny}"
+
+
+def tune_step(model: "lem.Model", steps: int = 3, use_cache: bool = True):
+    """Pick and set the fastest work decomposition of lem_step for this grid
+    (lem_set_tiling: the FP32 codes pass's chunks per band item, and whole or
+    half-height warp tiles), timed on copies of the model's own elevations;
+    returns ((band_chunks, half_tiles), {"<band>x<half>": ms per step}).  Every
+    choice computes the same receivers, masks and (while no tree needs the
+    pointer-jumping device tier) the same elevations."""
+    key = step_key(model)
+    cache = _load() if use_cache else {}
+    if key in cache:
+        k, hf = cache[key]["shape"]
+        lem.lem_set_tiling(model.ctx, k, hf)
+        return (k, hf), cache[key].get("ms", {})
+    saved = model.h.clone()
+    default_k, _ = lem.lem_get_tiling(model.ctx)
+    bands = sorted(set(STEP_BAND_CHUNKS) | {default_k}) if model.dtype == lem.LEM_F32 else [0]
+    stream = torch.cuda.current_stream()
+    timings = {}
+    for k in bands:
+        for hf in (0, 1):
+            model.h.copy_(saved)
+            lem.lem_set_tiling(model.ctx, k, hf)
+            model.step(1)  # warm-up
+            model.h.copy_(saved)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                model.step(1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            timings[f"{k}x{hf}"] = e0.elapsed_time(e1) / steps
+    best = min(timings, key=timings.get)
+    k, hf = (int(v) for v in best.split("x"))
+    model.h.copy_(saved)
+    lem.lem_set_tiling(model.ctx, k, hf)
+    model.sync()
+    if use_cache:
+        cache[key] = {"shape": [k, hf], "ms": timings}
+        _store(cache)
+    return (k, hf), timings

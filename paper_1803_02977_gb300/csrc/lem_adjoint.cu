@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(kBD, 1) adjoint_step_kernel(const __grid_const
   const bool lead = blockIdx.x == 0 && t == 0;
   if (lead) A.st->dev_roots[0] = 0;  // overflow flag of this step (read after a barrier)
   if (!phase_codes(A)) return;
+  if (ld_volatile(&A.st->err) != 0) return;  // a non-finite elevation: no outputs
   {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     const AdjTileQ q(dyn_smem + w * kWarpBytes);

@@ -182,6 +182,8 @@ StepArgs<HT, CT> make_args(lem_ctx* c, int phases, int nsteps) {
   a.tiles_x = (c->p.nx + kTileW - 1) / kTileW;
   a.ntiles = a.tiles_x * ((c->p.ny + tile_h<HT>() - 1) / tile_h<HT>());
   a.strip_rows = pick_strip_rows<HT>(c->p.nx, c->p.ny, c->grid * kWarps);
+  a.band_k = c->band_k > 0 ? c->band_k : pick_band_chunks(c->p.nx, c->p.ny, c->grid * kWarps);
+  a.half_tiles = c->half_tiles;
   a.has_tmap = c->tmap_ok ? 1 : 0;
   a.tmap = c->tmap;
   a.Udt = c->p.U * c->p.dt;
@@ -196,7 +198,49 @@ StepArgs<HT, CT> make_args(lem_ctx* c, int phases, int nsteps) {
   a.dxdn = c->dxdn;
   a.dfac = c->dfac;
   a.dfacd = c->dfacd;
+  a.jt = c->jt;
+  a.jab1 = c->jab1;
+  a.jp0 = c->jp0;
+  a.jp1 = c->jp1;
+  a.jstamp = c->jstamp;
+  // breadth-first levels before jumping: a device-wide level costs several
+  // microseconds, a jumping round over the whole grid grows with its size
+  a.jump_cap = c->N >> 15 > 64 ? c->N >> 15 : 64;
+  // with the jumping tier, forests deeper than 256 levels leave the block
+  // tier for it (a block-private level costs about a microsecond and more)
+  a.priv_levels = c->jt ? 256 : kMaxPrivLevels;
   return a;
+}
+
+// Scratch of the pointer-jumping device tier (lem_jump.cuh), allocated once:
+// tour words, a second (A, B) buffer, two pointer buffers, root stamps.
+int ensure_jump_scratch(lem_ctx* c) {
+  if (c->jt) return LEM_OK;
+  const size_t N = (size_t)c->N;
+  unsigned long long* jt = nullptr;
+  double2* ab = nullptr;
+  int *p0 = nullptr, *p1 = nullptr;
+  unsigned* stamp = nullptr;
+  cudaError_t e = cudaMalloc(&jt, 2 * N * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&ab, N * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&p0, N * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&p1, N * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&stamp, N * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(stamp, 0, N * sizeof(unsigned), c->stream);
+  if (e != cudaSuccess) {
+    cudaFree(jt);
+    cudaFree(ab);
+    cudaFree(p0);
+    cudaFree(p1);
+    cudaFree(stamp);
+    return cuda_status(e);
+  }
+  c->jt = jt;
+  c->jab1 = ab;
+  c->jp0 = p0;
+  c->jp1 = p1;
+  c->jstamp = stamp;
+  return LEM_OK;
 }
 
 template <typename HT, typename CT>
@@ -273,9 +317,11 @@ int encode_tmap(lem_ctx* c) {
   std::memset(&m, 0, sizeof(m));
   const cuuint64_t dims[2] = {(cuuint64_t)c->p.nx, (cuuint64_t)c->p.ny};
   const cuuint64_t strides[1] = {(cuuint64_t)pitch};
-  const int rows = esz == 8 ? pick_strip_rows<double>(c->p.nx, c->p.ny, c->grid * kWarps)
-                            : pick_strip_rows<float>(c->p.nx, c->p.ny, c->grid * kWarps);
-  const cuuint32_t box[2] = {(cuuint32_t)kStageCols, (cuuint32_t)(rows + 4)};
+  // FP64: the codes pass's strips (kStageCols x strip rows + 4); FP32: the
+  // chunks of its column bands (kChunkCols x kChunkRows)
+  const int rows = esz == 8 ? pick_strip_rows<double>(c->p.nx, c->p.ny, c->grid * kWarps) + 4
+                            : kChunkRows;
+  const cuuint32_t box[2] = {(cuuint32_t)(esz == 8 ? kStageCols : kChunkCols), (cuuint32_t)rows};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode(&m, esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
@@ -304,12 +350,13 @@ extern "C" {
 const char* lem_status_string(int s) {
   switch (s) {
     case LEM_OK: return "ok";
-    case LEM_EINVAL: return "invalid argument or receiver graph";
+    case LEM_EINVAL: return "invalid argument, receiver graph or non-finite elevation";
     case LEM_ENOMEM: return "device allocation failed";
     case LEM_ECUDA: return "CUDA runtime error";
     case LEM_ETIMEOUT: return "bounded device wait ran out";
     case LEM_ESTATE: return "stage called before its inputs were computed";
     case LEM_EOVERFLOW: return "grid too large for 32-bit cell addresses";
+    case LEM_EBOUNDS: return "index out of bounds (checked build)";
     default: return "unknown status";
   }
 }
@@ -443,6 +490,11 @@ void lem_destroy(lem_ctx* c) {
   cudaFree(c->mfd_norm);
   cudaFree(c->mfd_queue);
   cudaFree(c->mfd_state);
+  cudaFree(c->jt);
+  cudaFree(c->jab1);
+  cudaFree(c->jp0);
+  cudaFree(c->jp1);
+  cudaFree(c->jstamp);
   if (c->host_status) cudaFreeHost(c->host_status);
   delete c;
 }
@@ -476,6 +528,7 @@ int lem_receivers(lem_ctx* c, int32_t* dev_rec) {
   int rc = launch_step(c, kPhRec, 1);
   if (rc != LEM_OK) return rc;
   c->rec_valid = true;
+  c->graph_valid = true;
   c->lev_valid = c->acc_valid = false;
   if (dev_rec) {
     export_rec_kernel<<<aux_grid(c), 256, 0, c->stream>>>(c->code, dev_rec, c->N, c->p.nx);
@@ -551,6 +604,10 @@ int lem_step(lem_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return LEM_EINVAL;
   if (!c->h) return LEM_ESTATE;
   if (nsteps == 0) return LEM_OK;
+  if (c->mode == 0 && c->newton_iters == 0 && c->N < (1 << 30)) {
+    const int rj = ensure_jump_scratch(c);
+    if (rj != LEM_OK) return rj;
+  }
   if (c->fill_on) {
     // one step at a time: the depression flood, then the step
     for (int s = 0; s < nsteps; ++s) {
@@ -558,12 +615,14 @@ int lem_step(lem_ctx* c, int nsteps) {
       if (rc == LEM_OK) rc = launch_step(c, c->mode == 0 ? kPhTiles : kPhAll, 1);
       if (rc != LEM_OK) return rc;
     }
+    c->graph_valid = true;
     c->rec_valid = c->frozen;
     c->lev_valid = c->acc_valid = c->frozen && c->mode == 1;
     return LEM_OK;
   }
   int rc = launch_step(c, c->mode == 0 ? kPhTiles : kPhAll, nsteps);
   if (rc != LEM_OK) return rc;
+  c->graph_valid = true;
   // A frozen graph's codes and masks stay current; the device-wide queue and
   // counts are current only if the device-wide form ran (mode 1).
   c->rec_valid = c->frozen;
@@ -612,6 +671,98 @@ int lem_set_receivers(lem_ctx* c, const int32_t* dev_rec) {
   return LEM_OK;
 }
 
+int lem_last_graph(lem_ctx* c, int32_t* dev_rec, uint8_t* dev_mask) {
+  if (!c) return LEM_EINVAL;
+  if (!c->graph_valid) return LEM_ESTATE;
+  if (dev_rec) {
+    export_rec_kernel<<<aux_grid(c), 256, 0, c->stream>>>(c->code, dev_rec, c->N, c->p.nx);
+    LEM_CUDA(cudaGetLastError());
+  }
+  if (dev_mask)
+    LEM_CUDA(cudaMemcpyAsync(dev_mask, c->mask, (size_t)c->N, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  return LEM_OK;
+}
+
+// ---- checkpoint / resume --------------------------------------------------
+// A state blob: a header (format tag, grid, element type, steps taken, the
+// device tier's jumping hint) followed by the bound elevations.
+namespace {
+struct StateHeader {
+  uint32_t tag;        // 'LEMS'
+  uint32_t version;    // 1
+  int32_t nx, ny;
+  int32_t dtype;       // LEM_F64 or LEM_F32
+  int32_t jump_hint;   // the device tier starts with pointer jumping
+  int64_t steps;       // lem_step steps taken by the context (private + device-wide)
+};
+static_assert(sizeof(StateHeader) == 32, "state header layout");
+constexpr uint32_t kStateTag = 0x534D454Cu;  // "LEMS" in memory order
+
+size_t state_bytes(const lem_ctx* c) {
+  return sizeof(StateHeader) + (size_t)c->N * (c->p.dtype == LEM_F64 ? 8 : 4);
+}
+}  // namespace
+
+int lem_state_size(lem_ctx* c, int64_t* bytes) {
+  if (!c || !bytes) return LEM_EINVAL;
+  *bytes = (int64_t)state_bytes(c);
+  return LEM_OK;
+}
+
+int lem_get_state(lem_ctx* c, void* buf, int64_t bytes) {
+  if (!c || !buf) return LEM_EINVAL;
+  if (!c->h) return LEM_ESTATE;
+  if (bytes < (int64_t)state_bytes(c)) return LEM_EINVAL;
+  LEM_CUDA(cudaStreamSynchronize(c->stream));
+  int w[2] = {0, 0};
+  LEM_CUDA(cudaMemcpy(&w[0], (char*)c->st + offsetof(DevState, private_steps), sizeof(int),
+                      cudaMemcpyDeviceToHost));
+  LEM_CUDA(cudaMemcpy(&w[1], (char*)c->st + offsetof(DevState, global_steps), sizeof(int),
+                      cudaMemcpyDeviceToHost));
+  int hint = 0;
+  LEM_CUDA(cudaMemcpy(&hint, (char*)c->st + offsetof(DevState, jump_hint), sizeof(int),
+                      cudaMemcpyDeviceToHost));
+  StateHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  hd.tag = kStateTag;
+  hd.version = 1;
+  hd.nx = c->p.nx;
+  hd.ny = c->p.ny;
+  hd.dtype = c->p.dtype;
+  hd.jump_hint = hint;
+  hd.steps = (int64_t)w[0] + w[1];
+  LEM_CUDA(cudaMemcpy(buf, &hd, sizeof(hd), cudaMemcpyDefault));
+  LEM_CUDA(cudaMemcpy((char*)buf + sizeof(hd), c->h, state_bytes(c) - sizeof(hd),
+                      cudaMemcpyDefault));
+  return LEM_OK;
+}
+
+int lem_set_state(lem_ctx* c, const void* buf, int64_t bytes) {
+  if (!c || !buf) return LEM_EINVAL;
+  if (!c->h) return LEM_ESTATE;
+  if (bytes < (int64_t)state_bytes(c)) return LEM_EINVAL;
+  StateHeader hd;
+  LEM_CUDA(cudaMemcpy(&hd, buf, sizeof(hd), cudaMemcpyDefault));
+  if (hd.tag != kStateTag || hd.version != 1 || hd.nx != c->p.nx || hd.ny != c->p.ny ||
+      hd.dtype != c->p.dtype || hd.steps < 0 || (hd.jump_hint != 0 && hd.jump_hint != 1))
+    return LEM_EINVAL;
+  LEM_CUDA(cudaStreamSynchronize(c->stream));
+  LEM_CUDA(cudaMemcpy(c->h, (const char*)buf + sizeof(hd), state_bytes(c) - sizeof(hd),
+                      cudaMemcpyDefault));
+  // the step counter resumes as private steps (the split is not kept)
+  const int w[2] = {(int)hd.steps, 0};
+  LEM_CUDA(cudaMemcpy((char*)c->st + offsetof(DevState, private_steps), &w[0], sizeof(int),
+                      cudaMemcpyHostToDevice));
+  LEM_CUDA(cudaMemcpy((char*)c->st + offsetof(DevState, global_steps), &w[1], sizeof(int),
+                      cudaMemcpyHostToDevice));
+  LEM_CUDA(cudaMemcpy((char*)c->st + offsetof(DevState, jump_hint), &hd.jump_hint, sizeof(int),
+                      cudaMemcpyHostToDevice));
+  if (!c->frozen) c->rec_valid = false;
+  c->lev_valid = c->acc_valid = false;
+  return LEM_OK;
+}
+
 int lem_sync(lem_ctx* c) {
   if (!c) return LEM_EINVAL;
   return read_status(c, nullptr);
@@ -633,6 +784,22 @@ int lem_set_step_mode(lem_ctx* c, int mode) {
   return LEM_OK;
 }
 
+int lem_set_tiling(lem_ctx* c, int band_chunks, int half_tiles) {
+  if (!c || band_chunks < 0 || band_chunks == 1 || band_chunks > 16 ||
+      (half_tiles != 0 && half_tiles != 1))
+    return LEM_EINVAL;
+  c->band_k = band_chunks;
+  c->half_tiles = half_tiles;
+  return LEM_OK;
+}
+
+int lem_get_tiling(lem_ctx* c, int* band_chunks, int* half_tiles) {
+  if (!c || !band_chunks || !half_tiles) return LEM_EINVAL;
+  *band_chunks = c->band_k > 0 ? c->band_k : pick_band_chunks(c->p.nx, c->p.ny, c->grid * kWarps);
+  *half_tiles = c->half_tiles;
+  return LEM_OK;
+}
+
 int lem_step_stats(lem_ctx* c, int64_t* private_steps, int64_t* device_wide_steps) {
   if (!c) return LEM_EINVAL;
   LEM_CUDA(cudaStreamSynchronize(c->stream));
@@ -643,6 +810,19 @@ int lem_step_stats(lem_ctx* c, int64_t* private_steps, int64_t* device_wide_step
                       cudaMemcpyDeviceToHost));
   if (private_steps) *private_steps = v[0];
   if (device_wide_steps) *device_wide_steps = v[1];
+  return LEM_OK;
+}
+
+int lem_jump_stats(lem_ctx* c, int64_t* stats) {
+  if (!c || !stats) return LEM_EINVAL;
+  LEM_CUDA(cudaStreamSynchronize(c->stream));
+  int v[2] = {0, 0};
+  LEM_CUDA(cudaMemcpy(&v[0], (char*)c->st + offsetof(DevState, jump_steps), sizeof(int),
+                      cudaMemcpyDeviceToHost));
+  LEM_CUDA(cudaMemcpy(&v[1], (char*)c->st + offsetof(DevState, jump_rounds), sizeof(int),
+                      cudaMemcpyDeviceToHost));
+  stats[0] = v[0];
+  stats[1] = v[1];
   return LEM_OK;
 }
 

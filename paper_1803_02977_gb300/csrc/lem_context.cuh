@@ -32,9 +32,12 @@ struct lem_ctx {
   void* cntq = nullptr;    // counts in private-queue order
   int pcap = 0;
   int mode = 0;       // 0: block-private levels with fallback, 1: device-wide only
+  int band_k = 0;     // lem_set_tiling: FP32 codes-pass chunks per item (0: heuristic)
+  int half_tiles = 0; // lem_set_tiling: warp tier on half-height tiles
   int grid = 0;
   int* host_status = nullptr;  // pinned: [err, nlevels]
   bool rec_valid = false, lev_valid = false, acc_valid = false, frozen = false;
+  bool graph_valid = false;  // code/mask hold the graph of the last step or lem_receivers
   double Kdt = 0, dxd = 0, area_scale = 0;
   // Alg 6 for a general slope exponent (lem_set_slope_exponent); 0 updates =
   // the n = 1 closed form
@@ -54,6 +57,13 @@ struct lem_ctx {
   int* mfd_queue = nullptr;    // the levels, nx*ny
   void* mfd_state = nullptr;
   void* fill_state = nullptr;  // round counters
+  // the device tier's pointer-jumping form: scratch allocated by the first
+  // lem_step in step mode 0 (44 bytes per cell)
+  unsigned long long* jt = nullptr;  // 2 words per cell
+  double2* jab1 = nullptr;
+  int* jp0 = nullptr;
+  int* jp1 = nullptr;
+  unsigned* jstamp = nullptr;
   double wait_limit_s = 2.0;
   unsigned long long* trace = nullptr;  // device trace buffer (lem_trace_enable)
   lem::TmaDesc tmap{};      // TMA descriptor of the bound h (host copy)

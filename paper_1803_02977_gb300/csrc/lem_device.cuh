@@ -21,6 +21,18 @@ constexpr int kTableN = 1 << 16;
 // Status codes written into the device status word (same values as lem.h).
 constexpr int kErrInval = -1;
 constexpr int kErrTimeout = -4;
+constexpr int kErrBounds = -7;
+
+// Index checks of the LEM_DEBUG build (the library compiled with -DLEM_DEBUG,
+// liblem_debug.so): every guarded access checks its index against the array
+// it touches; one out of range records kErrBounds and is skipped -- never a
+// trap, so the kernel keeps its barriers and the context stays usable.  In
+// the regular build the checks compile away.
+#ifdef LEM_DEBUG
+constexpr bool kDebugChecks = true;
+#else
+constexpr bool kDebugChecks = false;
+#endif
 
 // Phase bits of the persistent step kernel.
 constexpr int kPhRec = 1;     // Alg 1 receivers + Alg 2 donor masks + level 0
@@ -66,7 +78,15 @@ struct DevState {
   int dev_roots[2];
   int covered[2];
   int tiles_next[2];  // warp-tier tiles claimed (zero between launches)
+  int ovf_count[2];   // warp-tier items that did not fit (listed for the block tier)
   unsigned long long tier_cells[3];  // cells handled by warp, block, device tier
+  // the device tier's pointer-jumping form (lem_jump.cuh)
+  int jump_epoch;        // stamp of the latest jumping step (root marks)
+  int jump_vote[3];      // per-round change votes
+  int jump_hint;         // the last device tier was deep: jump at once
+  int jump_rounds;       // erosion rounds of the latest jumping step
+  int jump_steps;        // steps whose device tier jumped
+  unsigned long long jump_step_cells;  // eroding cells of the latest jumping step
 };
 
 // Trace tags: phase in the high half, level (or 0) in the low half.
@@ -87,6 +107,11 @@ enum TraceTag : int {
   kTrStepEnd = 14 << 16,    // end-of-step barrier passed
   kTrLocal = 15 << 16,      // block 0 reached the next barrier (low half: which)
   kTrTilesEnd = 16 << 16,   // warp and block tiers done on every block (barrier passed)
+  kTrJumpTour = 17 << 16,   // pointer-jumping tier: tour links built
+  kTrJumpRank = 18 << 16,   // one list-ranking round (low half: round)
+  kTrJumpInit = 19 << 16,   // counts, factors and first affine maps
+  kTrJumpErode = 20 << 16,  // one erosion-jumping round (low half: round)
+  kTrBlockEnd = 21 << 16,   // block tier done on every block (barrier passed)
 };
 
 // Record a timestamp (block 0, thread 0 only; no-op when tracing is off).
@@ -118,6 +143,18 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 __device__ __forceinline__ void set_error(DevState* st, int code) { atomicCAS(&st->err, 0, code); }
+
+// True if 0 <= i < n; in the LEM_DEBUG build, false (with kErrBounds
+// recorded) otherwise.  The regular build always answers true.
+__device__ __forceinline__ bool in_bounds(DevState* st, long long i, long long n) {
+  if constexpr (kDebugChecks) {
+    if (i < 0 || i >= n) {
+      if (st) set_error(st, kErrBounds);
+      return false;
+    }
+  }
+  return true;
+}
 
 // Hint the memory system to bring the line holding p into L1.
 __device__ __forceinline__ void prefetch_l1(const void* p) {

@@ -153,6 +153,7 @@ struct TileErode {
 template <typename HT, bool kNewton = false>
 struct TileArgs {
   int nx, ny, tiles_x;
+  DevState* st = nullptr;  // index checks of the LEM_DEBUG build report here
   const uint8_t* code;
   const uint8_t* mask;
   HT* h;
@@ -266,6 +267,7 @@ __device__ __forceinline__ int tile_forest(const TileArgs<HT, kNewton>& a, const
         const int kk = __ffs(pm) - 1;
         const int pos = tail + e;
         const int cc = pc + off[kk];
+        if (!in_bounds(a.st, pos, Q::kCap) || !in_bounds(a.st, cc, (long long)nx * ny)) continue;
         q.c[pos] = cc;
         q.pd[pos] = (1u << 16) | ((unsigned)(head + s) << 4) | (unsigned)(7 - kk);
         cp_async_elem(q.v + pos, h + cc, true);
@@ -307,7 +309,7 @@ __device__ __forceinline__ int tile_forest(const TileArgs<HT, kNewton>& a, const
       const int c = q.c[jj];
       const unsigned pd = q.pd[jj];
       const HT hn = ero(c, (int)(pd & 15u), pd >> 16, q.v[jj], q.v[(pd >> 4) & 0xFFFu]);
-      hh[c] = hn;
+      if (in_bounds(a.st, c, (long long)nx * ny)) hh[c] = hn;
       q.v[jj] = hn;
     }
     __syncwarp();
@@ -327,6 +329,13 @@ __device__ __noinline__ int block_tier(const StepArgs<HT, CT>& a, Shared& s, int
   uint8_t* pqm = a.pqm + (size_t)b * a.pcap;
   uint8_t* pqk = a.pqk + (size_t)b * a.pcap;
   constexpr int TH = tile_h<HT>();
+  if (a.jt != nullptr && ld_volatile(&a.st->jump_hint) != 0) {
+    // the last device tier was deep: these trees go straight to it
+    for (int i = w; i < nov; i += kWarps)
+      push_tile_roots_device<TH>(a.code, a.queue, dev_roots, s.ovf_tiles[i], a.tiles_x, nx, ny,
+                                 lane);
+    return 0;
+  }
   for (int i = w; i < nov; i += kWarps) {
     int cd[TH], x, y0, tile, rlo, rhi;
     item_rows<TH>(s.ovf_tiles[i], &tile, &rlo, &rhi);
@@ -358,26 +367,24 @@ __device__ __noinline__ int block_tier(const StepArgs<HT, CT>& a, Shared& s, int
   return 0;
 }
 
-// The warp tier and the block tier of one step, for this block's share of
-// tiles.  Roots that neither tier can hold are appended to the device tier's
-// level 0 (queue, counter *dev_roots).  The cells handled are added to
-// *covered and to the per-tier totals.
+// The warp tier of one step.  Work items (tiles, or halves of the last
+// tiles) are claimed from a device-wide counter; an item whose forest does
+// not fit a warp is appended to the device-wide overflow list ovf[] (counter
+// *n_ovf) for the block tier.  The cells handled are added to *covered and
+// to the warp tier's total.
 template <typename HT, typename CT, bool kNewton>
 __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, int* tiles_next,
-                                         int* dev_roots, int* covered) {
+                                         int* n_ovf, int* ovf, int* covered) {
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   const TileQ<HT> q(dyn_smem + w * kWarpBytes);
-  if (t == 0) {
-    s.n_ovf = 0;
-    s.n0 = 0;
-  }
   if (t < 8) s.off[t] = nbr_off(t, a.nx);
   __syncthreads();
   TileArgs<HT, kNewton> ta;
   ta.nx = a.nx;
   ta.ny = a.ny;
   ta.tiles_x = a.tiles_x;
+  ta.st = a.st;
   ta.code = a.code;
   ta.mask = a.mask;
   ta.h = a.h;
@@ -405,10 +412,9 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
   // T - S are whole tiles; the last S tiles (one per four warps of the
   // grid) are claimed as halves, so the last claims are half as long.
   // Lane 0 maps a claim to its item (-1: none left).
-  constexpr int TH = tile_h<HT>();
   const auto item_of = [&](int claim) {
     const int T = a.ntiles;
-    const int S = min(T, (int)gridDim.x * (kWarps / 4)), TF = T - S;
+    const int S = a.half_tiles ? T : min(T, (int)gridDim.x * (kWarps / 4)), TF = T - S;
     if (claim >= T + S) return -1;
     return claim < TF ? tile_item(claim, 0)
                       : tile_item(TF + ((claim - TF) >> 1), 1 + ((claim - TF) & 1));
@@ -427,30 +433,60 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
       mine += r;
       continue;
     }
-    int i = 0;
-    if (lane == 0) i = atomicAdd(&s.n_ovf, 1);
-    i = __shfl_sync(0xffffffffu, i, 0);
-    if (i < kOvfCap) {
-      if (lane == 0) s.ovf_tiles[i] = cur;
-    } else {
-      push_tile_roots_device<TH>(a.code, a.queue, dev_roots, cur, a.tiles_x, a.nx, a.ny, lane);
-    }
+    if (lane == 0) ovf[atomicAdd(n_ovf, 1)] = cur;
   }
   // per-warp totals (lane 0's count is the warp's)
   if (lane == 0) s.wcount[w] = (int)mine;
   __syncthreads();
   trace_point(a.st, kTrLocal + 4);
-  long long by_warps = 0, by_block = 0;
-  if (t == 0)
-    for (int i = 0; i < kWarps; ++i) by_warps += s.wcount[i];
-
-  // block tier: the overflowed tiles' roots as level 0 of a private queue
-  const int nov = min(s.n_ovf, kOvfCap);
-  if (nov > 0) by_block = block_tier<HT, CT, kNewton>(a, s, nov, dev_roots);
-  trace_point(a.st, kTrLocal + 5);
   if (t == 0) {
-    atomicAdd(covered, (int)(by_warps + by_block));
+    long long by_warps = 0;
+    for (int i = 0; i < kWarps; ++i) by_warps += s.wcount[i];
+    atomicAdd(covered, (int)by_warps);
     atomicAdd(&a.st->tier_cells[0], (unsigned long long)by_warps);
+  }
+}
+
+// The block tier of one step, after a grid barrier: the n overflowed items
+// of the list ovf[] are owned by block (tile index mod grid size) -- a rule
+// that does not depend on which warp found them, so each block's forest,
+// and whether it fits, is the same in every run.  A block that owns more
+// than kOvfCap items hands all their roots to the device tier.
+template <typename HT, typename CT, bool kNewton>
+__device__ __noinline__ void phase_block_tier(const StepArgs<HT, CT>& a, Shared& s, int n,
+                                              const int* ovf, int* dev_roots, int* covered) {
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int b = blockIdx.x, G = (int)gridDim.x;
+  constexpr int TH = tile_h<HT>();
+  if (t == 0) {
+    s.n_ovf = 0;
+    s.n0 = 0;
+  }
+  if (t < 8) s.off[t] = nbr_off(t, a.nx);
+  __syncthreads();
+  for (int i = t; i < n; i += kBD) {
+    const int it = __ldcg(ovf + i);
+    if ((it >> 2) % G == b) {
+      const int k = atomicAdd(&s.n_ovf, 1);
+      if (k < kOvfCap) s.ovf_tiles[k] = it;
+    }
+  }
+  __syncthreads();
+  const int nov = s.n_ovf;
+  long long by_block = 0;
+  if (nov > kOvfCap) {
+    for (int i = t >> 5; i < n; i += kWarps) {
+      const int it = __ldcg(ovf + i);
+      if ((it >> 2) % G == b)
+        push_tile_roots_device<TH>(a.code, a.queue, dev_roots, it, a.tiles_x, a.nx, a.ny, lane);
+    }
+  } else if (nov > 0) {
+    by_block = block_tier<HT, CT, kNewton>(a, s, nov, dev_roots);
+  }
+  (void)w;
+  trace_point(a.st, kTrLocal + 5);
+  if (t == 0 && by_block > 0) {
+    atomicAdd(covered, (int)by_block);
     atomicAdd(&a.st->tier_cells[1], (unsigned long long)by_block);
   }
 }

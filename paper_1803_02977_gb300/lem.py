@@ -15,6 +15,7 @@ from . import build as _build
 
 LEM_OK, LEM_EINVAL, LEM_ENOMEM, LEM_ECUDA, LEM_ETIMEOUT, LEM_ESTATE, LEM_EOVERFLOW = \
     0, -1, -2, -3, -4, -5, -6
+LEM_EBOUNDS = -7
 LEM_F64, LEM_F32 = 0, 1
 
 _lib = None
@@ -81,12 +82,19 @@ SIGNATURES = [
     ("lem_set_fill", _I, [_VP, _I]),
     ("lem_fill_stats", _I, [_VP, _I64P]),
     ("lem_set_receivers", _I, [_VP, _VP]),
+    ("lem_last_graph", _I, [_VP, _VP, _VP]),
+    ("lem_state_size", _I, [_VP, _I64P]),
+    ("lem_get_state", _I, [_VP, _VP, ctypes.c_int64]),
+    ("lem_set_state", _I, [_VP, _VP, ctypes.c_int64]),
     ("lem_sync", _I, [_VP]),
     ("lem_set_wait_limit", _I, [_VP, _D]),
     ("lem_selftest_wait", _I, [_VP]),
     ("lem_set_step_mode", _I, [_VP, _I]),
+    ("lem_set_tiling", _I, [_VP, _I, _I]),
+    ("lem_get_tiling", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     ("lem_step_stats", _I, [_VP, _I64P, _I64P]),
     ("lem_tier_stats", _I, [_VP, _I64P]),
+    ("lem_jump_stats", _I, [_VP, _I64P]),
     ("lem_trace_enable", _I, [_VP, _I]),
     ("lem_trace_read", _I, [_VP, _VP, _VP, _I, ctypes.POINTER(_I)]),
     ("lem_adjoint", _I, [_VP, _VP, _VP, _I, _I, _VP, ctypes.POINTER(_D), _VP]),
@@ -107,7 +115,18 @@ LEM_NOALLOC_MAX_CELLS = 1 << 18
 TRACE_PHASES = {1: "start", 2: "receivers", 3: "level0", 4: "bfs_wide", 5: "bfs_narrow",
                 6: "acc_wide", 7: "acc_narrow", 8: "uplift", 9: "erode_wide",
                 10: "erode_narrow", 11: "private_levels", 12: "private_accumulate",
-                13: "private_erode", 14: "step_end", 15: "block0_done", 16: "tiles_end"}
+                13: "private_erode", 14: "step_end", 15: "block0_done", 16: "tiles_end",
+                17: "jump_tour", 18: "jump_rank", 19: "jump_init", 20: "jump_erode",
+                21: "block_end"}
+
+
+def _load(path):
+    L = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
 
 
 def lib(build_if_missing: bool = True):
@@ -119,13 +138,26 @@ def lib(build_if_missing: bool = True):
             path = _build.build()
         if not os.path.exists(path):
             raise ImportError(f"liblem.so is not built ({path}); run __graft_entry__.build()")
-        L = ctypes.CDLL(path)
-        for name, res, args in SIGNATURES:
-            f = getattr(L, name)
-            f.restype = res
-            f.argtypes = args
-        _lib = L
+        _lib = _load(path)
     return _lib
+
+
+class use_debug_library:
+    """Within this context every call of the binding goes to liblem_debug.so,
+    the build whose kernels check their indices (LEM_EBOUNDS on a failed
+    check, never a trap); contexts must be created and used inside it."""
+
+    def __enter__(self):
+        global _lib
+        path = _build.build(debug=True)
+        self.saved = _lib
+        _lib = _load(path)
+        return _lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
 
 
 def _check(status, where):
@@ -234,6 +266,30 @@ def lem_set_receivers(ctx, rec):
     _check(lib().lem_set_receivers(ctx, _ptr(rec)), "lem_set_receivers")
 
 
+def lem_last_graph(ctx, rec=None, mask=None):
+    _check(lib().lem_last_graph(ctx, _ptr(rec), _ptr(mask)), "lem_last_graph")
+
+
+def lem_state_size(ctx):
+    n = ctypes.c_int64(0)
+    _check(lib().lem_state_size(ctx, ctypes.byref(n)), "lem_state_size")
+    return n.value
+
+
+def lem_get_state(ctx):
+    """The context's state as a host numpy uint8 array (lem_get_state)."""
+    import numpy as np
+    buf = np.empty(lem_state_size(ctx), np.uint8)
+    _check(lib().lem_get_state(ctx, buf.ctypes.data_as(_VP), buf.size), "lem_get_state")
+    return buf
+
+
+def lem_set_state(ctx, buf):
+    import numpy as np
+    b = np.ascontiguousarray(buf, np.uint8)
+    _check(lib().lem_set_state(ctx, b.ctypes.data_as(_VP), b.size), "lem_set_state")
+
+
 def lem_sync(ctx):
     _check(lib().lem_sync(ctx), "lem_sync")
 
@@ -251,6 +307,17 @@ def lem_set_step_mode(ctx, mode):
     _check(lib().lem_set_step_mode(ctx, mode), "lem_set_step_mode")
 
 
+def lem_set_tiling(ctx, band_chunks=0, half_tiles=0):
+    _check(lib().lem_set_tiling(ctx, band_chunks, half_tiles), "lem_set_tiling")
+
+
+def lem_get_tiling(ctx):
+    """(band chunks of the FP32 codes pass, half-height warp tiles) in use."""
+    k, h = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().lem_get_tiling(ctx, ctypes.byref(k), ctypes.byref(h)), "lem_get_tiling")
+    return k.value, h.value
+
+
 def lem_step_stats(ctx):
     """(steps without device-wide levels, steps with them)."""
     p, g = ctypes.c_int64(0), ctypes.c_int64(0)
@@ -263,6 +330,13 @@ def lem_tier_stats(ctx):
     v = (ctypes.c_int64 * 3)()
     _check(lib().lem_tier_stats(ctx, v), "lem_tier_stats")
     return tuple(int(x) for x in v)
+
+
+def lem_jump_stats(ctx):
+    """(steps whose device tier used pointer jumping, erosion rounds of the latest)."""
+    v = (ctypes.c_int64 * 2)()
+    _check(lib().lem_jump_stats(ctx, v), "lem_jump_stats")
+    return int(v[0]), int(v[1])
 
 
 def lem_adjoint(ctx, h0, lambda_T, nsteps, ckpt_every, dLdU, lambda_0=None):
@@ -375,8 +449,11 @@ def lem_step_noalloc(h, dx, K, m, U, dt, nsteps, stream=None):
     if h.dtype != torch.float64:
         raise ValueError("lem_step_noalloc takes float64 elevations")
     ny, nx = h.shape
-    s = (stream or torch.cuda.current_stream()).cuda_stream
-    return lib().lem_step_noalloc(nx, ny, _ptr(h), dx, K, m, U, dt, nsteps, ctypes.c_void_p(s))
+    # the library launches on the current device: make it h's
+    with torch.cuda.device(h.device):
+        s = (stream or torch.cuda.current_stream(h.device)).cuda_stream
+        return lib().lem_step_noalloc(nx, ny, _ptr(h), dx, K, m, U, dt, nsteps,
+                                      ctypes.c_void_p(s))
 
 
 def lem_trace_enable(ctx, capacity):
@@ -472,6 +549,13 @@ class Model:
     def step(self, nsteps=1):
         with _nvtx("lem.step"):
             lem_step(self.ctx, nsteps)
+
+    def last_graph(self):
+        """(rec int32[N], donor mask uint8[N]) of the last step's receiver graph."""
+        rec = torch.empty(self.N, dtype=torch.int32, device=self.h.device)
+        msk = torch.empty(self.N, dtype=torch.uint8, device=self.h.device)
+        lem_last_graph(self.ctx, rec, msk)
+        return rec, msk
 
     def set_receivers(self, rec):
         lem_set_receivers(self.ctx, rec)

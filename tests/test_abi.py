@@ -38,7 +38,7 @@ def test_binding_covers_header():
 def test_status_strings(lib):
     from paper_1803_02977_gb300 import lem
     for code in (lem.LEM_OK, lem.LEM_EINVAL, lem.LEM_ENOMEM, lem.LEM_ECUDA, lem.LEM_ETIMEOUT,
-                 lem.LEM_ESTATE, lem.LEM_EOVERFLOW):
+                 lem.LEM_ESTATE, lem.LEM_EOVERFLOW, lem.LEM_EBOUNDS):
         s = lib.lem_status_string(code).decode()
         assert s and s != "unknown status"
 
@@ -83,3 +83,23 @@ def test_new_entry_points_reject_null_context_without_device_work(lib):
     stats = (ctypes.c_int64 * 4)()
     assert lib.lem_fill_stats(None, stats) == lem.LEM_EINVAL
     assert lib.lem_accumulate_mfd(None, c_d(1.0), None, c_vp(0), None) == lem.LEM_EINVAL
+
+
+def test_graph_state_and_jump_entry_points_reject_null_context(lib):
+    from paper_1803_02977_gb300 import lem
+    n = ctypes.c_int64(0)
+    stats = (ctypes.c_int64 * 2)()
+    assert lib.lem_last_graph(None, None, None) == lem.LEM_EINVAL
+    assert lib.lem_state_size(None, ctypes.byref(n)) == lem.LEM_EINVAL
+    assert lib.lem_get_state(None, ctypes.c_void_p(0), ctypes.c_int64(0)) == lem.LEM_EINVAL
+    assert lib.lem_set_state(None, ctypes.c_void_p(0), ctypes.c_int64(0)) == lem.LEM_EINVAL
+    assert lib.lem_jump_stats(None, stats) == lem.LEM_EINVAL
+
+
+def test_debug_library_builds_and_exports_the_same_symbols():
+    from paper_1803_02977_gb300 import build, lem
+    path = build.build(debug=True)
+    L = ctypes.CDLL(path)
+    for n in _declared("lem.h"):
+        assert hasattr(L, n), n
+    assert L.lem_step(None, 1) == lem.LEM_EINVAL
