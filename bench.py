@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="grid10000_f32")
+    ap.add_argument("--edge", type=int, default=0,
+                    help="run the workload's recipe on an edge x edge grid instead\n"
+                         "(smaller cases of the same kernel for profiling)")
     ap.add_argument("--flush-mib", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-phases", action="store_true")
@@ -205,7 +208,7 @@ def run_reference(args):
         return 0
     from paper_1803_02977_gb300 import synth
     import oracle
-    w = synth.workload(args.workload)
+    w = workload_of(synth, args)
     p = oracle_params(w)
     h = w.initial()
     # size each step so that warmup + steps end within a few minutes
@@ -239,6 +242,15 @@ def run_reference(args):
     return 0
 
 
+def workload_of(synth, args):
+    """The named workload, on an edge x edge grid if --edge is given."""
+    import dataclasses
+    w = synth.workload(args.workload)
+    if args.edge:
+        w = dataclasses.replace(w, name=f"{w.name}_edge{args.edge}", nx=args.edge, ny=args.edge)
+    return w
+
+
 def config_of(w, args):
     return {"workload": w.name, "nx": w.nx, "ny": w.ny, "dtype": w.dtype,
             "count_bits": 64 if w.area_dtype == "i64" else 32, "dx": w.dx, "K": w.K, "m": w.m,
@@ -258,7 +270,7 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = synth.workload(args.workload)
+    w = workload_of(synth, args)
     P = 8 if w.dtype == "f64" else 4
     Ab = 8 if w.area_dtype == "i64" else 4
     h0_np = w.initial().astype(np.float64 if P == 8 else np.float32)
@@ -269,6 +281,10 @@ def run_ours(args):
     mdl = lem.Model(h, **par)
     flush = torch.empty(args.flush_mib << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    # the step's work decomposition, picked by the autotuner on the initial
+    # surface (outside the timed region; the surface is left as it was)
+    from paper_1803_02977_gb300 import autotune
+    tiling, tiling_ms = autotune.tune_step(mdl, steps=3, use_cache=False)
 
     def barrier():
         if ws > 1:
@@ -371,7 +387,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
 
     forms = None
-    if not args.no_forms:
+    if not args.no_forms and not args.edge:
         forms = measure_forms(lem, synth, args, w, ms_per_step, flush, dev, ws, rank)
 
     cpu = None
@@ -404,6 +420,8 @@ def run_ours(args):
             "timeline": timeline,
             "tier_cell_fraction": {"warp_tiles": tier_frac[0], "block_queues": tier_frac[1],
                                    "device_wide": tier_frac[2]},
+            "tiling": {"strip_rows": tiling[0], "half_tiles": tiling[1],
+                       "autotune_ms_per_step": {k: round(v, 4) for k, v in tiling_ms.items()}},
             "clocks": clk, "e2e": e2e,
             "gpu_launches": K, "cpu_baseline": cpu, "forms": forms}
     if rank == 0:
@@ -448,29 +466,29 @@ def step_phase_split(timeline, tier_cells, ab, N, peak):
     return out
 
 
-def measure_e2e(lem, h0_np, par, dev, steps, ws):
+def measure_e2e(lem, h0_np, par, dev, steps, ws, nbuf=3):
     """End to end through the public API with host buffers: every step the
     elevations are copied from pinned host memory to the device, advanced one
     step by lem_step, and copied back to pinned host memory.  Copies and the
-    step run on three streams over two device buffers, so the upload of step
-    i+1 and the download of step i-1 overlap step i (the context is bound to
-    step i's buffer before its launch); the timed region spans the first
-    upload to the last download."""
+    step run on three streams over nbuf device buffers, so the upload of
+    step i+1 and the download of step i-1 overlap step i (the context is
+    bound to step i's buffer before its launch); the timed region spans the
+    first upload to the last download."""
     import torch
     import torch.distributed as dist
     hin = torch.from_numpy(np.ascontiguousarray(h0_np)).pin_memory()
-    hout = [torch.empty_like(hin).pin_memory() for _ in range(2)]
-    d = [torch.empty(hin.shape, dtype=hin.dtype, device=dev) for _ in range(2)]
+    hout = [torch.empty_like(hin).pin_memory() for _ in range(nbuf)]
+    d = [torch.empty(hin.shape, dtype=hin.dtype, device=dev) for _ in range(nbuf)]
     me = lem.Model(d[0], **par)
     comp = torch.cuda.current_stream()
     s_up, s_down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    up_done = [torch.cuda.Event() for _ in range(2)]
-    comp_done = [torch.cuda.Event() for _ in range(2)]
-    down_done = [torch.cuda.Event() for _ in range(2)]
+    up_done = [torch.cuda.Event() for _ in range(nbuf)]
+    comp_done = [torch.cuda.Event() for _ in range(nbuf)]
+    down_done = [torch.cuda.Event() for _ in range(nbuf)]
 
     def one(i):
-        b = i & 1
-        if i >= 2:
+        b = i % nbuf
+        if i >= nbuf:
             s_up.wait_event(down_done[b])  # buffer b's previous result has left
         with torch.cuda.stream(s_up):
             d[b].copy_(hin, non_blocking=True)
@@ -484,7 +502,7 @@ def measure_e2e(lem, h0_np, par, dev, steps, ws):
             hout[b].copy_(d[b], non_blocking=True)
             down_done[b].record(s_down)
 
-    for i in range(4):
+    for i in range(nbuf + 1):
         one(i)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -492,14 +510,15 @@ def measure_e2e(lem, h0_np, par, dev, steps, ws):
     s_up.wait_event(e0)
     for i in range(steps):
         one(i)
-    comp.wait_event(down_done[(steps - 1) & 1])
-    comp.wait_event(down_done[steps & 1])
+    for b in range(nbuf):
+        comp.wait_event(down_done[b])
     e1.record(comp)
     torch.cuda.synchronize()
     me.sync()
     ms = e0.elapsed_time(e1)
     # the result of the last step, checked to have left the device intact
-    ok = bool(torch.equal(hout[(steps - 1) & 1], d[(steps - 1) & 1].cpu()))
+    last = (steps - 1) % nbuf
+    ok = bool(torch.equal(hout[last], d[last].cpu()))
     me.close()
     te = torch.tensor([ms], dtype=torch.float64, device=dev)
     if ws > 1:
@@ -509,9 +528,8 @@ def measure_e2e(lem, h0_np, par, dev, steps, ws):
     return {"value": n * steps * ws / (float(te.item()) / 1e3), "unit": METRIC,
             "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": steps,
             "ms_per_step": float(te.item()) / steps, "result_copied_back": ok,
-            "how": "pinned host -> device, lem_step, device -> pinned host every step; "
-                   "three streams, two device buffers (upload i+1 and download i-1 "
-                   "overlap step i)"}
+            "how": f"pinned host -> device, lem_step, device -> pinned host every step; three "
+                   f"streams, {nbuf} device buffers (upload i+1 and download i-1 overlap step i)"}
 
 
 def measure_forms(lem, synth, args, w, ms_per_step, flush, dev, ws, rank):
@@ -820,7 +838,7 @@ def traced_step(lem, mdl, flush, nsteps=3):
             "steps_in_launch": nsteps, "raw": raw}
 
 
-STEP_KERNEL_SOURCES = ("lem_step_kernel.cuh", "lem_tiles.cuh", "lem_device.cuh",
+STEP_KERNEL_SOURCES = ("lem_step_kernel.cuh", "lem_tiles.cuh", "lem_jump.cuh", "lem_device.cuh",
                        "lem_context.cuh", "lem_api.cu")
 
 

@@ -304,10 +304,10 @@ LEM_API int lem_selftest_wait(lem_ctx* ctx);
 LEM_API int lem_set_step_mode(lem_ctx* ctx, int mode);
 
 /* Work decomposition of lem_step (mode 0), for the package's autotuner.
- *  band_chunks  FP32 elevations: the codes pass (Algs 1-2) takes work items
- *               of 30 columns x (8*band_chunks - 4) rows, staged in chunks of
- *               8 rows; 2 .. 16, or 0 for the default (the largest that
- *               leaves four items per warp).  FP64 elevations ignore it.
+ *  strip_rows   rows per strip of the codes pass (Algs 1-2; each warp takes
+ *               strips of 30 columns): 8, 16 or 32 (32 with FP32 elevations
+ *               only), or 0 for the default (32 for FP32 when every warp of
+ *               the grid gets two strips, else 16).
  *  half_tiles   1: the warp tier claims every 32-column tile as two
  *               half-height items (8 -> 4 rows with FP64 elevations, 12 -> 6
  *               with FP32); 0 (the default): only the last tiles of a step.
@@ -315,8 +315,8 @@ LEM_API int lem_set_step_mode(lem_ctx* ctx, int mode);
  * while no tree needs the device tier's pointer-jumping form (whose sums
  * associate differently, within a few units in the last place).
  * LEM_EINVAL for other values.  lem_get_tiling returns the values in use. */
-LEM_API int lem_set_tiling(lem_ctx* ctx, int band_chunks, int half_tiles);
-LEM_API int lem_get_tiling(lem_ctx* ctx, int* band_chunks, int* half_tiles);
+LEM_API int lem_set_tiling(lem_ctx* ctx, int strip_rows, int half_tiles);
+LEM_API int lem_get_tiling(lem_ctx* ctx, int* strip_rows, int* half_tiles);
 
 /* Number of lem_step steps completed without and with device-wide levels
  * since the context was created (synchronises). */

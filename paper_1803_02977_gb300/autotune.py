@@ -2,8 +2,8 @@
 
 tune_batch times every supported (threads per block, entries per thread)
 shape of the batched form on a copy of the batch's own elevations; tune_step
-times the single-grid step's tilings (lem_set_tiling: rows per work item of
-the FP32 codes pass, whole or half-height warp tiles).  Each keeps the
+times the single-grid step's tilings (lem_set_tiling: rows per strip of the
+codes pass, whole or half-height warp tiles).  Each keeps the
 fastest and caches the choice in a JSON file keyed by GPU name and the
 problem (the batch's size profile -- number of realizations and a log2
 histogram of their cell counts -- or the grid's size and types), so later
@@ -93,7 +93,9 @@ def tune_batch(batch: "lem.Batch", steps: int = 2, use_cache: bool = True):
 
 # ---- the single-grid step (lem_set_tiling) ------------------------------------
 
-STEP_BAND_CHUNKS = (2, 4, 6, 8, 11, 14, 16)
+def step_strip_rows(model: "lem.Model"):
+    """Rows per strip of the codes pass that the step accepts for this grid."""
+    return (8, 16, 32) if model.dtype == lem.LEM_F32 else (8, 16)
 
 
 def step_key(model: "lem.Model") -> str:
@@ -104,10 +106,10 @@ def step_key(model: "lem.Model") -> str:
 
 def tune_step(model: "lem.Model", steps: int = 3, use_cache: bool = True):
     """Pick and set the fastest work decomposition of lem_step for this grid
-    (lem_set_tiling: the FP32 codes pass's chunks per band item, and whole or
-    half-height warp tiles), timed on copies of the model's own elevations;
-    returns ((band_chunks, half_tiles), {"<band>x<half>": ms per step}).  Every
-    choice computes the same receivers, masks and (while no tree needs the
+    (lem_set_tiling: rows per strip of the codes pass, whole or half-height
+    warp tiles), timed on copies of the model's own elevations; returns
+    ((strip_rows, half_tiles), {"<rows>x<half>": ms per step}).  Every choice
+    computes the same receivers, masks and (while no tree needs the
     pointer-jumping device tier) the same elevations."""
     key = step_key(model)
     cache = _load() if use_cache else {}
@@ -116,11 +118,9 @@ def tune_step(model: "lem.Model", steps: int = 3, use_cache: bool = True):
         lem.lem_set_tiling(model.ctx, k, hf)
         return (k, hf), cache[key].get("ms", {})
     saved = model.h.clone()
-    default_k, _ = lem.lem_get_tiling(model.ctx)
-    bands = sorted(set(STEP_BAND_CHUNKS) | {default_k}) if model.dtype == lem.LEM_F32 else [0]
     stream = torch.cuda.current_stream()
     timings = {}
-    for k in bands:
+    for k in step_strip_rows(model):
         for hf in (0, 1):
             model.h.copy_(saved)
             lem.lem_set_tiling(model.ctx, k, hf)

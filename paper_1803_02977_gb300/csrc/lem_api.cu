@@ -149,6 +149,14 @@ const void* kernel_for(const lem_ctx* c, bool newton) {
   return c64 ? step_kernel_ptr<float, long long>(newton) : step_kernel_ptr<float, int>(newton);
 }
 
+// Rows per strip of the codes pass: the lem_set_tiling choice, else the
+// heuristic (pick_strip_rows).
+int strip_rows_of(const lem_ctx* c) {
+  if (c->strip_rows > 0) return c->strip_rows;
+  return c->p.dtype == LEM_F64 ? pick_strip_rows<double>(c->p.nx, c->p.ny, c->grid * kWarps)
+                               : pick_strip_rows<float>(c->p.nx, c->p.ny, c->grid * kWarps);
+}
+
 template <typename HT, typename CT>
 StepArgs<HT, CT> make_args(lem_ctx* c, int phases, int nsteps) {
   StepArgs<HT, CT> a;
@@ -181,8 +189,7 @@ StepArgs<HT, CT> make_args(lem_ctx* c, int phases, int nsteps) {
   a.pcap = c->pcap;
   a.tiles_x = (c->p.nx + kTileW - 1) / kTileW;
   a.ntiles = a.tiles_x * ((c->p.ny + tile_h<HT>() - 1) / tile_h<HT>());
-  a.strip_rows = pick_strip_rows<HT>(c->p.nx, c->p.ny, c->grid * kWarps);
-  a.band_k = c->band_k > 0 ? c->band_k : pick_band_chunks(c->p.nx, c->p.ny, c->grid * kWarps);
+  a.strip_rows = strip_rows_of(c);
   a.half_tiles = c->half_tiles;
   a.has_tmap = c->tmap_ok ? 1 : 0;
   a.tmap = c->tmap;
@@ -317,11 +324,8 @@ int encode_tmap(lem_ctx* c) {
   std::memset(&m, 0, sizeof(m));
   const cuuint64_t dims[2] = {(cuuint64_t)c->p.nx, (cuuint64_t)c->p.ny};
   const cuuint64_t strides[1] = {(cuuint64_t)pitch};
-  // FP64: the codes pass's strips (kStageCols x strip rows + 4); FP32: the
-  // chunks of its column bands (kChunkCols x kChunkRows)
-  const int rows = esz == 8 ? pick_strip_rows<double>(c->p.nx, c->p.ny, c->grid * kWarps) + 4
-                            : kChunkRows;
-  const cuuint32_t box[2] = {(cuuint32_t)(esz == 8 ? kStageCols : kChunkCols), (cuuint32_t)rows};
+  const int rows = strip_rows_of(c) + 4;
+  const cuuint32_t box[2] = {(cuuint32_t)kStageCols, (cuuint32_t)rows};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode(&m, esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
@@ -784,18 +788,19 @@ int lem_set_step_mode(lem_ctx* c, int mode) {
   return LEM_OK;
 }
 
-int lem_set_tiling(lem_ctx* c, int band_chunks, int half_tiles) {
-  if (!c || band_chunks < 0 || band_chunks == 1 || band_chunks > 16 ||
-      (half_tiles != 0 && half_tiles != 1))
-    return LEM_EINVAL;
-  c->band_k = band_chunks;
+int lem_set_tiling(lem_ctx* c, int rows, int half_tiles) {
+  if (!c || (half_tiles != 0 && half_tiles != 1)) return LEM_EINVAL;
+  const int most = c->p.dtype == LEM_F64 ? lem::strip_rows<double>() : lem::strip_rows<float>();
+  if (rows != 0 && rows != 8 && rows != 16 && rows != 32) return LEM_EINVAL;
+  if (rows > most) return LEM_EINVAL;
+  c->strip_rows = rows;
   c->half_tiles = half_tiles;
-  return LEM_OK;
+  return encode_tmap(c);  // the strips' TMA box follows the rows
 }
 
-int lem_get_tiling(lem_ctx* c, int* band_chunks, int* half_tiles) {
-  if (!c || !band_chunks || !half_tiles) return LEM_EINVAL;
-  *band_chunks = c->band_k > 0 ? c->band_k : pick_band_chunks(c->p.nx, c->p.ny, c->grid * kWarps);
+int lem_get_tiling(lem_ctx* c, int* rows, int* half_tiles) {
+  if (!c || !rows || !half_tiles) return LEM_EINVAL;
+  *rows = strip_rows_of(c);
   *half_tiles = c->half_tiles;
   return LEM_OK;
 }

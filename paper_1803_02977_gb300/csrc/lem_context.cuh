@@ -32,7 +32,7 @@ struct lem_ctx {
   void* cntq = nullptr;    // counts in private-queue order
   int pcap = 0;
   int mode = 0;       // 0: block-private levels with fallback, 1: device-wide only
-  int band_k = 0;     // lem_set_tiling: FP32 codes-pass chunks per item (0: heuristic)
+  int strip_rows = 0; // lem_set_tiling: rows per strip of the codes pass (0: heuristic)
   int half_tiles = 0; // lem_set_tiling: warp tier on half-height tiles
   int grid = 0;
   int* host_status = nullptr;  // pinned: [err, nlevels]

@@ -67,7 +67,6 @@ struct StepArgs {
   int pcap;             // entries per block in pq
   int tiles_x, ntiles;  // warp-tier tiles per row, in total
   int strip_rows;       // owned rows per strip of the codes pass (pick_strip_rows)
-  int band_k;           // FP32 codes pass: TMA chunks per band item (pick_band_chunks)
   int half_tiles;       // warp tier: every tile claimed as two half-height items
   int has_tmap;         // tmap describes h (else strips are staged element-wise)
   TmaDesc tmap;         // TMA descriptor of h: 2-D box of kStageCols x (strip_rows + 4)
@@ -356,7 +355,11 @@ __device__ __forceinline__ int receiver_f32_fast(const float hc, const float* v)
   return undecided ? -1 : code;
 }
 
-__device__ __forceinline__ int receiver_code_f32_vals(const float hc, const float* v) {
+// st: where a non-finite value among the nine is reported (kErrInval); the
+// check runs only on the path that such values take (bit patterns at or
+// above that of +inf, which negative values share).
+__device__ __forceinline__ int receiver_code_f32_vals(const float hc, const float* v,
+                                                      DevState* st = nullptr) {
   {
     const int k = receiver_f32_fast(hc, v);
     if (k >= 0) return k;
@@ -364,6 +367,12 @@ __device__ __forceinline__ int receiver_code_f32_vals(const float hc, const floa
   unsigned worst = Bits<float>::of(hc);
 #pragma unroll
   for (int k = 0; k < 8; ++k) worst = max(worst, Bits<float>::of(v[k]));
+  if (worst >= Bits<float>::kInf && st) {
+    bool fin = isfinite(hc);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) fin = fin && isfinite(v[k]);
+    if (!fin) set_error(st, kErrInval);
+  }
   if (worst < Bits<float>::kInf) {
     const float mC = fminf(fminf(v[1], v[3]), fminf(v[4], v[6]));
     const float mD = fminf(fminf(v[0], v[2]), fminf(v[5], v[7]));
@@ -397,9 +406,9 @@ __device__ __forceinline__ int receiver_code_f32_vals(const float hc, const floa
 // Alg 1 for an interior cell of elevation hc with neighbour elevations
 // v[0..7] (k order).
 template <typename HT>
-__device__ __forceinline__ int receiver_from(const HT hc, const HT* v) {
+__device__ __forceinline__ int receiver_from(const HT hc, const HT* v, DevState* st = nullptr) {
   if constexpr (sizeof(HT) == 4) {
-    return receiver_code_f32_vals(hc, v);
+    return receiver_code_f32_vals(hc, v, st);
   } else {
     return receiver_code_vals(hc, v);
   }
@@ -1014,9 +1023,10 @@ __device__ __forceinline__ void codes_strip(const HT* S, uint8_t* code, uint8_t*
           cd = kEdge;
         } else {
           const HT v[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
-          cd = receiver_from(mc, v);
+          cd = receiver_from(mc, v, st);
         }
-        if (own && y >= y0 && y < y1 && in_bounds(st, at, (long long)nx * ny)) code[at] = (uint8_t)cd;
+        if (own && y >= y0 && y < y1 && in_bounds(st, at, (long long)nx * ny))
+          code[at] = (uint8_t)cd;
       }
       ul = ml; uc = mc; ur = mr;
       ml = dl; mc = dc; mr = dr;
@@ -1029,287 +1039,6 @@ __device__ __forceinline__ void codes_strip(const HT* S, uint8_t* code, uint8_t*
     if (own && y > y0 && y <= y1 && in_bounds(st, at - nx, (long long)nx * ny))
       mask[at - nx] = (uint8_t)mask_from_pointers(pl, pw, pr);
   }
-}
-
-// ---- Algs 1-2 for FP32 elevations: column bands through a ring of TMA chunks ----
-//
-// A warp takes work items of one band of kBandOwn owned columns by R rows
-// (R = 8k - 4 for k chunks per item, band_rows).  Lane l computes the receiver
-// code of column X + l (X = first owned column - 1; lanes 1..30 own theirs),
-// walking down the rows with a 3-row window in registers; the elevations
-// arrive in chunks of kChunkRows rows x kChunkCols columns by 2-D TMA into a
-// ring of kRing chunk buffers in the warp's slice of shared memory, so that
-// several chunk loads are in flight while the warp computes (the next item's
-// first chunks are loaded while the current item ends).  Each item stages two
-// halo rows above and below its owned rows: codes are computed for one halo
-// row on each side, so the donor mask of every owned cell (Alg 2) follows
-// from the codes of its 3x3 neighbourhood, exchanged by shuffles.
-//
-// Per cell the receiver is decided in FP32 from the group minima, which the
-// 3-row window shares between rows: the minimum of each row's left and right
-// neighbour (one pair per row) serves the cell below as its NW/NE pair, the
-// cell itself as W/E and the cell above as SW/SE.  Ties keep the lowest k.
-// The decision is exact (equal to the FP64 comparison of Alg 1) whenever the
-// values are non-negative and finite, both group minima lie within 27
-// binades of h_c, h_c >= 2^-60, and the two groups' FP32 slopes differ by
-// more than 2^-18 (relative): then distinct floats give distinct FP64
-// slopes, so the group argmins are the FP64 ones, and the FP32 slopes
-// (within 2^-23 of the FP64 ones) order the groups.  Any other cell takes
-// Alg 1's reference form in FP64.  Non-finite elevations are reported as
-// kErrInval.
-constexpr int kBandOwn = 30;     // owned columns per band (lanes 1..30)
-constexpr int kChunkCols = 40;   // staged columns: X - 1 rounded down to 16 bytes, 40 wide
-constexpr int kChunkRows = 8;    // staged rows per chunk (the TMA box height)
-constexpr int kRing = 4;         // chunk buffers per warp (a power of two)
-constexpr int kChunkBytes = kChunkCols * kChunkRows * (int)sizeof(float);
-static_assert(kRing * kChunkBytes + kRing * 8 <= kWarpBytes, "the ring fits a warp slice");
-static_assert(kChunkBytes % 128 == 0 && kWarpBytes % 128 == 0, "chunk buffers 128-byte aligned");
-static_assert((kRing & (kRing - 1)) == 0, "ring index by masking");
-
-__host__ __device__ __forceinline__ int band_rows(int k) { return kChunkRows * k - 4; }
-
-// Chunks per work item: the largest k in 2..16 that still leaves sixteen
-// items per warp of the grid (fewer, larger items cost less halo; many of
-// them keep the warps of a block, which claim items one at a time, finishing
-// close together).
-__host__ __device__ __forceinline__ int pick_band_chunks(int nx, int ny, int warps) {
-  const long long nb = (nx + kBandOwn - 1) / kBandOwn;
-  int best = 2;
-  for (int k = 3; k <= 16; ++k) {
-    const long long items = nb * ((ny + band_rows(k) - 1) / band_rows(k));
-    if (items >= 16LL * warps) best = k;
-  }
-  return best;
-}
-
-// Alg 1 for a cell whose three rows of neighbours are summarised as: pu/pd
-// the minima of the NW,NE / SW,SE pairs, eu/ed whether the east member of
-// each is strictly lower, n/sv the N and S values, pm/em the W,E pair.
-// Returns the code; *undecided when the FP32 decision cannot be trusted.
-__device__ __forceinline__ int code_f32_fast(float hc, float pu, int eu, float n, float pm, int em,
-                                             float sv, float pd, int ed, bool* undecided) {
-  const float mD = fminf(pu, pd);
-  const float mC = fminf(pm, fminf(n, sv));
-  const float sC = __fsub_rn(hc, mC);
-  const float sD = __fmul_rn(__fsub_rn(hc, mD), 0.70710677f);
-  const bool cW = sC > __fmul_rn(sD, 1.000003814697265625f);
-  const bool dW = sD > __fmul_rn(sC, 1.000003814697265625f);
-  const bool pos = fmaxf(sC, sD) > 0.0f;
-  const unsigned bc = __float_as_uint(hc);
-  const unsigned bm = min(__float_as_uint(mC), __float_as_uint(mD));
-  const bool safe = (int)(bc - bm) < (27 << 23) && bc >= 0x21800000u;  // h_c >= 2^-60
-  *undecided = !safe || (pos && !cW && !dW);
-  const int kC = n == mC ? 1 : (pm == mC ? 3 + em : 6);
-  const int kD = pu <= pd ? 2 * eu : 5 + 2 * ed;
-  return pos ? (cW ? kC : kD) : kSink;
-}
-
-// Alg 1's reference form for one cell of FP32 elevations (promoted to
-// FP64), for the cells the fast decision leaves undecided; with `check`,
-// a non-finite value among the nine is recorded as kErrInval.
-__device__ __forceinline__ int code_f32_reference(float hc, float v0, float v1, float v2, float v3,
-                                                  float v4, float v5, float v6, float v7,
-                                                  bool check, DevState* st) {
-  const float v[8] = {v0, v1, v2, v3, v4, v5, v6, v7};
-  const double h = (double)hc;
-  double smax = 0.0;
-  int best = kSink;
-  bool fin = isfinite(hc);
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    fin = fin && isfinite(v[k]);
-    const double d = __dsub_rn(h, (double)v[k]);
-    const double sl = nbr_diag(k) ? __dmul_rn(d, kInvSqrt2) : d;
-    if (sl > smax) {
-      smax = sl;
-      best = k;
-    }
-  }
-  if (check && !fin) set_error(st, kErrInval);
-  return best;
-}
-
-// Reverse pointer byte of a code: bit 7-k for a receiver at neighbour k, so
-// that a neighbour at direction k of a cell contributes bit k to that cell's
-// donor mask exactly when it drains into it.  No receiver (8, 9): 0.
-__device__ __forceinline__ unsigned rev_pointer(int cd) { return 0x80u >> cd; }
-
-// Donor mask from the reverse pointer bytes (byte 0 row above, 1 own row, 2
-// row below) of the left column, this column and the right column; the
-// three contributions occupy disjoint bits, so adding the bytes ORs them.
-__device__ __forceinline__ unsigned mask_from_rev(unsigned l, unsigned m, unsigned r) {
-  const unsigned v = (l & 0x200801u) | (m & 0x400002u) | (r & 0x801004u);
-  return ((v * 0x10101u) >> 16) & 0xFFu;
-}
-
-// Stage chunk rows [y, y + kChunkRows) x columns [xb, xb + kChunkCols) of h
-// into buf with per-element asynchronous copies (zero outside the grid).
-__device__ __forceinline__ void stage_chunk(const float* h, int nx, int ny, int xb, int y,
-                                            float* buf, int lane) {
-  __syncwarp();  // every lane has read the buffer's previous chunk
-  for (int i = lane; i < kChunkRows * kChunkCols; i += 32) {
-    const int r = i / kChunkCols, col = i - r * kChunkCols;
-    const int xx = xb + col, yy = y + r;
-    const bool in = xx >= 0 && xx < nx && yy >= 0 && yy < ny;
-    cp_async_elem(buf + i, in ? h + ((size_t)yy * nx + xx) : h, in);
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  __syncwarp();
-}
-
-// Algs 1-2 over this block's share of the band items, by one warp (see
-// above).  Chunk g of the warp's stream of chunks (K per item) goes to ring
-// buffer g % kRing; it is waited for at its first row, and at the third row
-// of chunk g the buffer of chunk g - 1 (no row of the window lies in it any
-// more) is refilled with chunk g - 1 + kRing.  Items are claimed ahead as
-// the stream reaches them (at most three held).  Returns false if a bounded
-// wait ran out.
-template <typename CT>
-__device__ __noinline__ bool codes_bands_f32(const StepArgs<float, CT>& a, unsigned char* slice,
-                                             int lane, int* s_next, int u1) {
-  const int nx = a.nx, ny = a.ny;
-  DevState* const st = a.st;
-  const int K = a.band_k;
-  const int R = band_rows(K);
-  const int nb = (nx + kBandOwn - 1) / kBandOwn;
-  float* const ring = reinterpret_cast<float*>(slice);
-  unsigned long long* const bars =
-      reinterpret_cast<unsigned long long*>(slice + kRing * kChunkBytes);
-  const bool tma = a.has_tmap && (smem_u32(slice) & 127u) == 0;
-  if (tma && lane == 0)
-    for (int i = 0; i < kRing; ++i) mbar_init(bars + i, 1);
-  __syncwarp();
-  auto claim = [&]() {
-    int u = 0;
-    if (lane == 0) u = atomicAdd(s_next, 1);
-    return __shfl_sync(0xffffffffu, u, 0);
-  };
-  // the claimed items: q0 (current), q1, q2; nq of them claimed
-  int q0 = claim(), q1 = u1, q2 = u1, nq = 1;
-  int base = 0, gi = 0;  // stream index of q0's first chunk; chunks issued
-  // issue chunk g of the stream (false once the items are exhausted)
-  auto issue = [&](int g) {
-    const int idx = (g - base) / K;  // 0, 1 or 2
-    while (nq <= idx) {
-      const int u = nq == 1 ? q0 : q1;  // the last claimed item
-      const int v = u < u1 ? claim() : u1;
-      if (nq == 1) q1 = v; else q2 = v;
-      ++nq;
-    }
-    const int item = idx == 0 ? q0 : (idx == 1 ? q1 : q2);
-    if (item >= u1) return false;
-    const int j = g - base - idx * K;
-    const int sy = item / nb, sx = item - sy * nb;
-    if (lane == 0) {
-      const int buf = g & (kRing - 1);
-      fence_proxy_async_smem();  // earlier reads of this buffer come first
-      mbar_expect_tx(bars + buf, (unsigned)kChunkBytes);
-      tma_load_2d(ring + buf * (kChunkBytes / 4), &a.tmap, (kBandOwn * sx - 2) & ~3,
-                  R * sy - 2 + kChunkRows * j, bars + buf);
-    }
-    return true;
-  };
-  if (tma)
-    while (gi < kRing - 1 && issue(gi)) ++gi;
-  bool ok = true;
-  while (ok && q0 < u1) {
-    const int sy = q0 / nb, sx = q0 - sy * nb;
-    const int y0 = R * sy;                         // first owned row
-    const int x = kBandOwn * sx - 1 + lane;        // this lane's column
-    const int xb = (kBandOwn * sx - 2) & ~3;       // first staged column
-    const int sc = x - xb;                         // its staged column (1 .. 36)
-    const bool xin = x >= 0 && x < nx;
-    const bool xpe = x == 0 || x == nx - 1;
-    const bool own = lane >= 1 && lane <= kBandOwn && xin;
-    // the staged columns this lane reads lie inside a chunk row
-    in_bounds(st, sc - 1, kChunkCols);
-    in_bounds(st, sc + 1, kChunkCols);
-    // the window: per row the centre value b, the pair minimum p = min(left,
-    // right) and the pair bit e = [right < left]; rows up (u) and mid (m);
-    // eb packs ue (bit 0) and me (bit 1); bad holds one bit per window row
-    // with a negative or non-finite value in this lane's three columns
-    float ub = 0, mb = 0, up = 0, mp = 0;
-    unsigned eb = 0, bad = 0;
-    unsigned pw = 0;  // reverse pointer bytes of rows y-2, y-1, y
-    size_t at = (size_t)(long long)(y0 - 3) * nx + x;  // cell (x, y) of the middle row y
-    const int rows = R + 4;
-    for (int s = 0; s < rows; ++s, at += nx) {
-      const int r = s & (kChunkRows - 1);
-      const int g = base + s / kChunkRows;
-      if (r == 0) {
-        if (tma) {
-          ok = __all_sync(0xffffffffu, mbar_wait(bars + (g & (kRing - 1)), (unsigned)((g / kRing) & 1), st));
-          if (!ok) break;
-        } else {
-          stage_chunk(a.h, nx, ny, xb, y0 - 2 + s, ring + (g & (kRing - 1)) * (kChunkBytes / 4), lane);
-        }
-      } else if (r == 2 && tma && gi == g - 1 + kRing) {
-        __syncwarp();  // no lane reads chunk g - 1 any more
-        if (issue(gi)) ++gi;
-      }
-      const float* row = ring + (g & (kRing - 1)) * (kChunkBytes / 4) + r * kChunkCols + sc;
-      const float nl = row[-1], nbv = row[0], nr = row[1];
-      const float np = fminf(nl, nr);
-      const unsigned ne = nr < nl ? 1u : 0u;
-      const unsigned nrm = max(max(__float_as_uint(nl), __float_as_uint(nbv)), __float_as_uint(nr));
-      bad = ((bad << 1) | (nrm >= 0x7F800000u ? 1u : 0u)) & 7u;
-      if (s >= 2) {
-        const int y = y0 - 3 + s;  // the middle row
-        const bool in = xin && y >= 0 && y < ny;
-        const bool pe = xpe || y == 0 || y == ny - 1;
-        bool und;
-        int k = code_f32_fast(mb, up, (int)(eb & 1u), ub, mp, (int)(eb >> 1), nbv, np, (int)ne,
-                              &und);
-        // the rare cells the fast decision leaves open, behind a warp-uniform
-        // branch so that the FP64 reference form is not executed for the others
-        const bool need = (und || bad != 0) && in && !pe;
-        if (__builtin_expect(__any_sync(0xffffffffu, need), 0)) {
-          if (need) {
-            const int gu = base + (s - 2) / kChunkRows, gm = base + (s - 1) / kChunkRows;
-            const float* u = ring + (gu & (kRing - 1)) * (kChunkBytes / 4) +
-                             ((s - 2) & (kChunkRows - 1)) * kChunkCols + sc;
-            const float* m = ring + (gm & (kRing - 1)) * (kChunkBytes / 4) +
-                             ((s - 1) & (kChunkRows - 1)) * kChunkCols + sc;
-            k = code_f32_reference(m[0], u[-1], u[0], u[1], m[-1], m[1], nl, nbv, nr, bad != 0,
-                                   st);
-          }
-        }
-        k = !in ? kSink : (pe ? kEdge : k);
-        if (own && y >= y0 && y < y0 + R && y < ny && in_bounds(st, (long long)at, a.N))
-          a.code[at] = (uint8_t)k;
-        pw = (pw >> 8) | (rev_pointer(k) << 16);
-        if (s >= 3) {
-          // donor mask of row y - 1
-          const unsigned pl = __shfl_up_sync(0xffffffffu, pw, 1);
-          const unsigned pr = __shfl_down_sync(0xffffffffu, pw, 1);
-          const int ym = y - 1;
-          if (own && ym >= y0 && ym < y0 + R && ym < ny && in_bounds(st, (long long)(at - nx), a.N))
-            a.mask[at - nx] = (uint8_t)mask_from_rev(pl, pw, pr);
-        }
-      }
-      ub = mb;
-      mb = nbv;
-      up = mp;
-      mp = np;
-      eb = (eb >> 1) | (ne << 1);
-    }
-    if (!ok) break;
-    // the next item becomes current (claimed now if it was not yet)
-    base += K;
-    q0 = q1;
-    q1 = q2;
-    q2 = u1;
-    if (--nq == 0) {
-      q0 = claim();  // the item just finished was below u1
-      nq = 1;
-    }
-    __syncwarp();
-  }
-  __syncwarp();
-  if (tma && lane == 0 && ok)
-    for (int i = 0; i < kRing; ++i) mbar_inval(bars + i);
-  return ok;
 }
 
 template <typename HT, typename CT>
@@ -1331,13 +1060,8 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
   uint8_t* const code = a.code;
   uint8_t* const mask = a.mask;
   DevState* const st = a.st;
-  // FP32 elevations (not frozen): column bands through a TMA chunk ring
-  constexpr bool kBands = sizeof(HT) == 4;
-  const bool bands = kBands && !frozen;
   const int nsx = (nx + kStripOut - 1) / kStripOut;
-  const int units = bands ? ((nx + kBandOwn - 1) / kBandOwn) *
-                                ((ny + band_rows(a.band_k) - 1) / band_rows(a.band_k))
-                          : nsx * ((ny + kRows - 1) / kRows);
+  const int units = nsx * ((ny + kRows - 1) / kRows);
   // each block takes an equal contiguous range of strips, its warps claim
   // them one at a time (the next claim issued before the current strip)
   __shared__ int s_next;
@@ -1345,17 +1069,6 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
   const int u1 = (int)((long long)units * (b + 1) / G);
   if (threadIdx.x == 0) s_next = (int)((long long)units * b / G);
   __syncthreads();
-  if constexpr (kBands) {
-    if (bands) {
-      const bool okb = codes_bands_f32(a, dyn_smem + w * kWarpBytes, lane, &s_next, u1);
-      (void)okb;  // a wait that ran out recorded kErrTimeout: the barrier abandons
-      __syncthreads();
-      trace_point(a.st, kTrLocal + 1);
-      if (!grid_barrier(a.st, gridDim.x)) return false;
-      trace_point(a.st, kTrCodes);
-      return true;
-    }
-  }
   int u = 0;
   if (lane == 0) u = atomicAdd(&s_next, 1);
   u = __shfl_sync(0xffffffffu, u, 0);

@@ -424,11 +424,11 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
   item = __shfl_sync(0xffffffffu, item, 0);
   while (item >= 0) {
     int next = 0;
-    if (lane == 0) next = atomicAdd(tiles_next, 1);
+    if (lane == 0) next = item_of(atomicAdd(tiles_next, 1));
+    next = __shfl_sync(0xffffffffu, next, 0);
     const int r = tile_forest(ta, q, s.off, item, lane);
-    if (lane == 0) next = item_of(next);
     const int cur = item;
-    item = __shfl_sync(0xffffffffu, next, 0);
+    item = next;
     if (r >= 0) {
       mine += r;
       continue;

@@ -307,12 +307,12 @@ def lem_set_step_mode(ctx, mode):
     _check(lib().lem_set_step_mode(ctx, mode), "lem_set_step_mode")
 
 
-def lem_set_tiling(ctx, band_chunks=0, half_tiles=0):
-    _check(lib().lem_set_tiling(ctx, band_chunks, half_tiles), "lem_set_tiling")
+def lem_set_tiling(ctx, strip_rows=0, half_tiles=0):
+    _check(lib().lem_set_tiling(ctx, strip_rows, half_tiles), "lem_set_tiling")
 
 
 def lem_get_tiling(ctx):
-    """(band chunks of the FP32 codes pass, half-height warp tiles) in use."""
+    """(rows per strip of the codes pass, half-height warp tiles) in use."""
     k, h = ctypes.c_int(0), ctypes.c_int(0)
     _check(lib().lem_get_tiling(ctx, ctypes.byref(k), ctypes.byref(h)), "lem_get_tiling")
     return k.value, h.value

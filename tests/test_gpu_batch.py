@@ -96,7 +96,7 @@ def test_autotuner_picks_a_shape_and_keeps_results(tmp_path, monkeypatch):
 
 
 def test_step_tilings_agree_and_tuner_lists_them(tmp_path, monkeypatch):
-    """Every tiling of the single-grid step (rows per item of the FP32 codes
+    """Every tiling of the single-grid step (rows per strip of the codes
     pass, whole or half warp tiles) gives the same elevations on a grid whose
     trees fit the warp and block tiers; the tuner times every one."""
     from paper_1803_02977_gb300 import autotune, lem
@@ -105,12 +105,13 @@ def test_step_tilings_agree_and_tuner_lists_them(tmp_path, monkeypatch):
     for npt in (np.float32, np.float64):
         h0 = synth.noise_surface(517, 389, 9, south_tilt=1e-4).astype(npt)
         ref = None
-        bands = autotune.STEP_BAND_CHUNKS if npt == np.float32 else (0,)
-        for k in bands:
+        rows = (8, 16, 32) if npt == np.float32 else (8, 16)
+        for k in rows:
             for hf in (0, 1):
                 h = torch.tensor(h0, device=dev)
                 m = lem.Model(h)
                 lem.lem_set_tiling(m.ctx, k, hf)
+                assert lem.lem_get_tiling(m.ctx) == (k, hf)
                 m.step(3)
                 m.sync()
                 assert lem.lem_jump_stats(m.ctx)[0] == 0
@@ -120,8 +121,12 @@ def test_step_tilings_agree_and_tuner_lists_them(tmp_path, monkeypatch):
                 assert torch.equal(h.cpu(), ref), (npt, k, hf)
         h = torch.tensor(h0, device=dev)
         m = lem.Model(h)
+        if npt == np.float64:
+            with pytest.raises(lem.LemError):
+                lem.lem_set_tiling(m.ctx, 32, 0)  # FP64 strips hold at most 16 rows
         (k, hf), table = autotune.tune_step(m, steps=1)
-        assert len(table) >= 2 * len(bands)  # every band choice, whole and half tiles
-        assert f"{k}x{hf}" in table and table[f"{k}x{hf}"] == min(table.values())
+        assert sorted(table) == sorted(f"{r}x{f}" for r in rows for f in (0, 1))
+        assert table[f"{k}x{hf}"] == min(table.values())
+        assert lem.lem_get_tiling(m.ctx) == (k, hf)
         assert torch.equal(h, torch.tensor(h0, device=dev))  # tuning left h as it was
         m.close()

@@ -43,6 +43,8 @@ CASES = [
     ("tilted_1500x64", lambda npt: _tilted(1500, 64, 7).astype(npt)),
     ("filled_noise_400x300", lambda npt: _filled_noise(400, 300, 12, npt)),
     ("filled_noise_1024", lambda npt: _filled_noise(1024, 1024, 13, npt)),
+    # the 2048^2 workload's surface after depression filling (~3100 levels)
+    ("filled_grid2048", lambda npt: oracle.fill(synth.workload("grid2048_f64").initial().astype(npt))),
 ]
 
 
