@@ -156,10 +156,6 @@ __device__ __forceinline__ bool in_bounds(DevState* st, long long i, long long n
   return true;
 }
 
-// Hint the memory system to bring the line holding p into L1.
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
 
 // Device-wide barrier for a co-resident (cooperative) grid.  Thread 0 of each
 // block arrives on a counter; the last arrival resets it and advances the

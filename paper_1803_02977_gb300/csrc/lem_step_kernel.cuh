@@ -414,79 +414,6 @@ __device__ __forceinline__ int receiver_from(const HT hc, const HT* v, DevState*
   }
 }
 
-// Alg 1 for interior cell c, elevations read from h.
-template <typename HT>
-__device__ __forceinline__ int receiver_of(const HT* __restrict__ h, int c, int nx) {
-  HT v[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) v[k] = h[c + nbr_off(k, nx)];
-  return receiver_from(h[c], v);
-}
-
-// Alg 2 for one cell (perimeter included): bit k set iff neighbour k is in
-// the grid and its receiver code points back at this cell (code 7-k).
-__device__ __forceinline__ int donor_mask(const uint8_t* __restrict__ code, int c, int x, int y,
-                                          int nx, int ny) {
-  int msk = 0;
-  if (x > 0 && y > 0 && x < nx - 1 && y < ny - 1) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (code[c + nbr_off(k, nx)] == 7 - k) msk |= 1 << k;
-  } else {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int xn = x + nbr_dx(k), yn = y + nbr_dy(k);
-      if (xn >= 0 && yn >= 0 && xn < nx && yn < ny)
-        if (code[c + nbr_off(k, nx)] == 7 - k) msk |= 1 << k;
-    }
-  }
-  return msk;
-}
-
-// The 12 receiver-code bytes around code[p], read as three aligned words;
-// at(dx) returns the 4 codes code[p+dx .. p+dx+3] (dx in {-1, 0, 1}) as one
-// word.  The code array carries 16 guard bytes of 0xFF on both sides, so the
-// loads stay in bounds for every row with a row above and below.
-struct CodeRow {
-  unsigned w0, w1, w2;
-  int off;  // byte offset of code[p-1] within w0
-  __device__ __forceinline__ CodeRow(const uint8_t* code, int p) {
-    const int q = p - 1;
-    const int al = q & ~3;
-    off = q - al;
-    const unsigned* wp = reinterpret_cast<const unsigned*>(code + al);
-    w0 = wp[0];
-    w1 = wp[1];
-    w2 = wp[2];
-  }
-  __device__ __forceinline__ unsigned at(int dx) const {
-    const int s = off + 1 + dx;  // 0..5
-    return s < 4 ? __funnelshift_r(w0, w1, 8 * s) : __funnelshift_r(w1, w2, 8 * (s - 4));
-  }
-};
-
-// Alg 2 for the four cells c..c+3 of one row band (c a multiple of 4, all
-// four with a row above and below): bit k of byte i of *mword is set iff
-// neighbour k of cell c+i drains into it (code 7-k); *cword gets their codes.
-// Neighbours that wrap across a row end are perimeter cells (code 9) or guard
-// bytes (0xFF), which never match.
-__device__ __forceinline__ void donor_masks4(const uint8_t* __restrict__ code, int c, int nx,
-                                             unsigned* mword, unsigned* cword) {
-  const CodeRow up(code, c - nx), mid(code, c), dn(code, c + nx);
-  unsigned m = 0;
-  const unsigned ones = 0x01010101u;
-  m |= __vcmpeq4(up.at(-1), 7u * ones) & (0x01u * ones);   // k=0 NW
-  m |= __vcmpeq4(up.at(0), 6u * ones) & (0x02u * ones);    // k=1 N
-  m |= __vcmpeq4(up.at(1), 5u * ones) & (0x04u * ones);    // k=2 NE
-  m |= __vcmpeq4(mid.at(-1), 4u * ones) & (0x08u * ones);  // k=3 W
-  m |= __vcmpeq4(mid.at(1), 3u * ones) & (0x10u * ones);   // k=4 E
-  m |= __vcmpeq4(dn.at(-1), 2u * ones) & (0x20u * ones);   // k=5 SW
-  m |= __vcmpeq4(dn.at(0), 1u * ones) & (0x40u * ones);    // k=6 S
-  m |= __vcmpeq4(dn.at(1), 0u * ones) & (0x80u * ones);    // k=7 SE
-  *mword = m;
-  *cword = mid.at(0);
-}
-
 // ---- Alg 5 + Alg 6 -------------------------------------------------------------
 
 template <typename HT, typename CT>
@@ -722,47 +649,6 @@ __device__ __forceinline__ void warp_range(int N, int G, int b, int w, int* w0, 
   *w1 = min(c1, *w0 + wchunk);
 }
 
-// Alg 1 over cells [w0, w1) by one warp (or, for a frozen graph, a read of
-// the codes); returns the number of those cells without receiver.
-template <typename HT, typename CT>
-__device__ __forceinline__ int codes_sweep(const StepArgs<HT, CT>& a, int w0, int w1, int lane) {
-  const int nx = a.nx, ny = a.ny, N = a.N;
-  int wcnt = 0;
-  int x = w0 + lane, y = 0;
-  if (w0 < w1) {
-    y = x / nx;
-    x -= y * nx;
-  }
-  for (int base = w0; base < w1; base += 32) {
-    const int c = base + lane;
-    // the three rows two iterations ahead, into L1 (in-grid addresses only)
-    const int cp = c + 64;
-    if (!a.frozen && cp < w1 && cp > nx && cp + nx < N) {
-      prefetch_l1(a.h + (cp - nx));
-      prefetch_l1(a.h + cp);
-      prefetch_l1(a.h + (cp + nx));
-    }
-    int code = kEdge;
-    if (c < w1) {
-      if (!a.frozen) {
-        const bool perim = (x == 0 || y == 0 || x == nx - 1 || y == ny - 1);
-        code = perim ? kEdge : receiver_of(a.h, c, nx);
-        a.code[c] = (uint8_t)code;
-        if (!isfinite(a.h[c])) set_error(a.st, kErrInval);  // non-finite elevations are rejected
-      } else {
-        code = a.code[c];
-      }
-    }
-    wcnt += __popc(__ballot_sync(0xffffffffu, c < w1 && no_receiver(code)));
-    x += 32;
-    while (x >= nx) {
-      x -= nx;
-      ++y;
-    }
-  }
-  return wcnt;
-}
-
 // Algs 1-2 for the tiered step.  A warp owns a strip of kStripOut columns
 // and strip_rows() rows at a time.  It first stages the elevations the strip
 // needs (two rows and columns of halo on each side) into its slice of shared
@@ -984,6 +870,56 @@ __device__ __forceinline__ void codes_strip_f64(const double* S, uint8_t* code, 
   }
 }
 
+// codes_strip for FP32 elevations: two rows per iteration, as the FP64 form
+// (their decisions are independent, so the scheduler can interleave them);
+// the fast FP32 decision, and the exact one for the cells it leaves open
+// behind a warp-uniform branch (which also reports non-finite values).
+__device__ __forceinline__ void codes_strip_f32(const float* S, uint8_t* code, uint8_t* mask,
+                                                int nx, int ny, int x, int y0, int y1, bool xin,
+                                                bool xperim, bool own, int sc, DevState* st) {
+  const int yb = y0 - 2;
+  auto el = [&](int r, int col) -> float { return S[r * kStageCols + col]; };
+  float ul = el(0, sc - 1), uc = el(0, sc), ur = el(0, sc + 1);
+  float ml = el(1, sc - 1), mc = el(1, sc), mr = el(1, sc + 1);
+  long long at = (long long)(y0 - 1) * nx + x;
+  unsigned pw = 0;
+  for (int y = y0 - 1; y <= y1; y += 2, at += 2 * (long long)nx) {
+    const bool two = y + 1 <= y1;  // the same for the whole warp
+    const int r = y + 1 - yb;      // staged row below row y
+    const int r2 = two ? r + 1 : r;
+    const float dl = el(r, sc - 1), dc = el(r, sc), dr = el(r, sc + 1);
+    const float fl = el(r2, sc - 1), fc = el(r2, sc), fr = el(r2, sc + 1);
+    const float v0[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
+    const float v1[8] = {ml, mc, mr, dl, dr, fl, fc, fr};
+    int c0 = receiver_f32_fast(mc, v0);
+    int c1 = receiver_f32_fast(dc, v1);
+    const bool in0 = xin && y >= 0 && y < ny;
+    const bool in1 = two && xin && y + 1 < ny;  // y + 1 >= 0 always
+    c0 = !in0 ? 0xFF : ((xperim || y == 0 || y == ny - 1) ? kEdge : c0);
+    c1 = !in1 ? 0xFF : ((xperim || y + 1 == 0 || y + 1 == ny - 1) ? kEdge : c1);
+    if (__builtin_expect(__any_sync(0xffffffffu, c0 < 0 || c1 < 0), 0)) {
+      if (c0 < 0) c0 = receiver_code_f32_vals(mc, v0, st);
+      if (c1 < 0) c1 = receiver_code_f32_vals(dc, v1, st);
+    }
+    const long long N = (long long)nx * ny;
+    if (own && in0 && y >= y0 && y < y1 && in_bounds(st, at, N)) code[at] = (uint8_t)c0;
+    if (own && in1 && y + 1 < y1 && in_bounds(st, at + nx, N)) code[at + nx] = (uint8_t)c1;
+    pw = ((pw >> 8) & 0xFFFFu) | (pointer_bits(c0) << 16);
+    unsigned pl = __shfl_up_sync(0xffffffffu, pw, 1);
+    unsigned pr = __shfl_down_sync(0xffffffffu, pw, 1);
+    if (own && y > y0 && y <= y1 && in_bounds(st, at - nx, N))
+      mask[at - nx] = (uint8_t)mask_from_pointers(pl, pw, pr);
+    if (two) {
+      pw = ((pw >> 8) & 0xFFFFu) | (pointer_bits(c1) << 16);
+      pl = __shfl_up_sync(0xffffffffu, pw, 1);
+      pr = __shfl_down_sync(0xffffffffu, pw, 1);
+      if (own && y + 1 > y0 && in_bounds(st, at, N)) mask[at] = (uint8_t)mask_from_pointers(pl, pw, pr);
+    }
+    ul = dl; uc = dc; ur = dr;
+    ml = fl; mc = fc; mr = fr;
+  }
+}
+
 template <typename HT>
 __device__ __forceinline__ void codes_strip(const HT* S, uint8_t* code, uint8_t* mask, int nx,
                                             int ny, int x0, int y0, int rows, int xb, bool frozen,
@@ -997,6 +933,12 @@ __device__ __forceinline__ void codes_strip(const HT* S, uint8_t* code, uint8_t*
   if constexpr (sizeof(HT) == 8) {
     if (!frozen) {
       codes_strip_f64(reinterpret_cast<const double*>(S), code, mask, nx, ny, x, y0, y1, xin,
+                      xperim, own, sc, st);
+      return;
+    }
+  } else {
+    if (!frozen && st) {
+      codes_strip_f32(reinterpret_cast<const float*>(S), code, mask, nx, ny, x, y0, y1, xin,
                       xperim, own, sc, st);
       return;
     }
@@ -1119,17 +1061,39 @@ __device__ __noinline__ bool phase_codes(const StepArgs<HT, CT>& a) {
   return true;
 }
 
-// Algs 1-2 and level 0 of Alg 3 (the stage calls and the device-wide form).
-// Returns false if a barrier was abandoned.
+// The codes of cells c .. c+3 (c a multiple of 4) as one word, bytes beyond
+// the nv cells in range zero.
+__device__ __forceinline__ unsigned code_word(const uint8_t* code, int c, int nv) {
+  if (nv >= 4) return *reinterpret_cast<const unsigned*>(code + c);
+  unsigned w = 0;
+  for (int i = 0; i < nv; ++i) w |= (unsigned)code[c + i] << (8 * i);
+  return w;
+}
+
+// Algs 1-2 and level 0 of Alg 3 (the stage calls and the device-wide form):
+// the codes pass of the tiered step (TMA-staged strips, phase_codes) writes
+// the codes and donor masks; then the cells without receiver are listed in
+// ascending address order as level 0, each warp counting and then listing
+// its contiguous range.  Returns false if a barrier was abandoned.
 template <typename HT, typename CT>
 __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& s) {
   const unsigned G = gridDim.x;
   const int b = blockIdx.x, t = threadIdx.x, w = t >> 5, lane = t & 31;
-  const int nx = a.nx, ny = a.ny, N = a.N;
+  const int N = a.N;
+  if (!phase_codes(a)) return false;  // ends with a grid barrier
   int w0, w1;
   warp_range(N, (int)G, b, w, &w0, &w1);
-  // receiver codes and the count of cells without receiver, per warp
-  const int wcnt = codes_sweep(a, w0, w1, lane);
+  // the count of cells without receiver (code >= 8), per warp; four cells per
+  // lane per round (w0 is a multiple of 4)
+  int wcnt = 0;
+  for (int base = w0; base < w1; base += 128) {
+    const int c = base + 4 * lane;
+    const int nv = max(0, min(4, w1 - c));
+    const unsigned valid = nv >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nv)) - 1u);
+    wcnt += __popc(__vcmpgeu4(code_word(a.code, c, nv), 0x08080808u) & valid) >> 3;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wcnt += __shfl_down_sync(0xffffffffu, wcnt, o);
   if (lane == 0) s.wcount[w] = wcnt;
   __syncthreads();
   if (t == 0) {
@@ -1137,38 +1101,21 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
     for (int i = 0; i < kWarps; ++i) tot += s.wcount[i];
     a.partial[b] = tot;
   }
-  trace_point(a.st, kTrLocal + 1);
+  trace_point(a.st, kTrLocal + 2);
   if (!grid_barrier(a.st, G)) return false;
-  trace_point(a.st, kTrCodes);
 
   int prefix, total;
   block_prefix_of_partials<kBD>(a.partial, (int)G, b, &prefix, &total, s.sum);
   int wpre = 0;
   for (int i = 0; i < w; ++i) wpre += s.wcount[i];
-  // donor masks, and the cells without receiver, ascending, as level 0
+  // the cells without receiver, ascending, as level 0
   {
-    // Each lane takes 4 consecutive cells (w0 is a multiple of 4): their
-    // masks are built as one 32-bit word, byte by byte in parallel.
     int run = wpre;
     for (int base = w0; base < w1; base += 128) {
       const int c = base + 4 * lane;
-      const int nv = max(0, min(4, w1 - c));  // cells of this lane in range
-      unsigned mword = 0, cword = 0;           // masks, codes (byte i: cell c+i)
-      if (nv == 4 && c >= nx && c + 3 + nx < N) {
-        donor_masks4(a.code, c, nx, &mword, &cword);
-        *reinterpret_cast<unsigned*>(a.mask + c) = mword;
-      } else {
-        for (int i = 0; i < nv; ++i) {
-          const int ci = c + i, y = ci / nx, x = ci - y * nx;
-          const unsigned msk = donor_mask(a.code, ci, x, y, nx, ny);
-          a.mask[ci] = (uint8_t)msk;
-          mword |= msk << (8 * i);
-          cword |= (unsigned)a.code[ci] << (8 * i);
-        }
-      }
-      // cells without receiver (code >= 8): 0xFF bytes, in-range cells only
+      const int nv = max(0, min(4, w1 - c));
       const unsigned valid = nv >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nv)) - 1u);
-      const unsigned f = __vcmpgeu4(cword, 0x08080808u) & valid;
+      const unsigned f = __vcmpgeu4(code_word(a.code, c, nv), 0x08080808u) & valid;
       const int cnt = __popc(f) >> 3;
       int incl = cnt;
 #pragma unroll
@@ -1180,7 +1127,7 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         if ((f >> (8 * i)) & 1u) {
-          a.queue[prefix + pos] = c + i;
+          if (in_bounds(a.st, prefix + pos, N)) a.queue[prefix + pos] = c + i;
           ++pos;
         }
       }
@@ -1192,7 +1139,7 @@ __device__ __noinline__ bool phase_receivers(const StepArgs<HT, CT>& a, Shared& 
     a.levels[1] = total;
   }
   __syncthreads();
-  trace_point(a.st, kTrLocal + 2);
+  trace_point(a.st, kTrLocal + 3);
   if (!grid_barrier(a.st, G)) return false;
   trace_point(a.st, kTrLevel0);
   return true;
