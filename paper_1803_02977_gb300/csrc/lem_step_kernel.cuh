@@ -937,7 +937,7 @@ __device__ __forceinline__ void codes_strip(const HT* S, uint8_t* code, uint8_t*
       return;
     }
   } else {
-    if (!frozen && st) {
+    if (!frozen) {
       codes_strip_f32(reinterpret_cast<const float*>(S), code, mask, nx, ny, x, y0, y1, xin,
                       xperim, own, sc, st);
       return;
