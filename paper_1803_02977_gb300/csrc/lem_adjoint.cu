@@ -196,16 +196,11 @@ __device__ __forceinline__ int tile_adjoint(const AdjArgs& a, const AdjTileQ& q,
         const int v = __shfl_sync(0xffffffffu, incl, s + step - 1);
         if (v <= e) s += step;
       }
-      int pm = __shfl_sync(0xffffffffu, msk, s);
+      const int pm = __shfl_sync(0xffffffffu, msk, s);
       const int pc = __shfl_sync(0xffffffffu, c, s);
       const int pex = __shfl_sync(0xffffffffu, incl - k, s);
       if (e < tot) {
-        const int r = e - pex;
-        if (r > 0) pm &= pm - 1;
-        if (r > 1) pm &= pm - 1;
-        if (r > 2) pm &= pm - 1;
-        for (int t = 3; t < r; ++t) pm &= pm - 1;
-        const int kk = __ffs(pm) - 1;
+        const int kk = g_nth[pm * 8 + (e - pex)];
         const int pos = tail + e;
         const int cc = pc + off[kk];
         q.c[pos] = cc;
@@ -299,6 +294,7 @@ __global__ void __launch_bounds__(kBD, 1) adjoint_step_kernel(const __grid_const
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     const AdjTileQ q(dyn_smem + w * kWarpBytes);
     if (t < 8) s.off[t] = nbr_off(t, A.nx);
+    fill_nth(t, kBD);
     __syncthreads();
     const int ntiles = A.tiles_x * ((A.ny + kAdjTileH - 1) / kAdjTileH);
     int tile = 0;

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(BD) lem_batch_kernel(BatchArgs a) {
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   float* S = reinterpret_cast<float*>(dyn_smem + w * kWarpBytes);
   const TileQ<float> q(dyn_smem + w * kWarpBytes);
+  fill_nth(t, BD);  // read after the block barrier below
   while (true) {
     if (t == 0) {
       const int i = atomicAdd(a.next, 1);

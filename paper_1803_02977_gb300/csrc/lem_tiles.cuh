@@ -50,6 +50,20 @@ struct TileQ {
   }
 };
 
+// g_nth[m * 8 + r]: the position of the r-th lowest set bit (r = 0, 1, ...)
+// of the 8-bit donor mask m, 0 where m has no such bit.  A window of Alg 3
+// hands each lane one donor as "bit r of its parent's mask"; one lookup
+// replaces clearing r bits one at a time.  One table per block, filled by
+// fill_nth (all threads, then a block barrier) before the first forest.
+static __shared__ unsigned char g_nth[256 * 8];
+__device__ __forceinline__ void fill_nth(int t, int nthreads) {
+  for (int i = t; i < 256 * 8; i += nthreads) {
+    unsigned m = (unsigned)i >> 3;
+    for (int r = 0; r < (i & 7); ++r) m &= m - 1u;
+    g_nth[i] = (unsigned char)(m ? __ffs(m) - 1 : 0);
+  }
+}
+
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -170,36 +184,65 @@ __device__ __forceinline__ int tile_forest(const TileArgs<HT, kNewton>& a, const
   // the arguments used in the loops, held in registers (stores through other
   // pointers would otherwise force reloads)
   const int nx = a.nx, ny = a.ny, tiles_x = a.tiles_x;
-  const unsigned lt = (1u << lane) - 1u;
   const uint8_t* const mask = a.mask;
   const uint8_t* const code = a.code;
   const HT* const h = a.h;
-  // level 0: the item's cells without receiver, in row order
+  // level 0: the item's cells without receiver, in row order.  The tile's
+  // codes are read as 4-byte words (8 per row; lane l takes words l, l + 32,
+  // ...), and one scan of the words' root counts (packed in 10-bit fields)
+  // places every root.  In-grid codes are 0..9, so a root is a byte with
+  // bit 3 set; bytes outside the grid or the item's rows read as 0.
   int n = 0;
   {
     const int tile = item >> 2, part = item & 3;
     const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
     constexpr int TH = tile_h<HT>();
-    const int x = tx * kTileW + lane, y0 = ty * TH;
-    int cd[TH];
+    constexpr int kWords = TH * kTileW / 4 / 32;  // code words per lane
+    static_assert(TH * kTileW % 128 == 0 && kWords <= 3, "whole words per lane, 10-bit fields");
+    const int x0 = tx * kTileW, y0 = ty * TH;
+    const int rlo = part == 2 ? TH / 2 : 0, rhi = part == 1 ? TH / 2 : TH;
+    unsigned roots[kWords];
+    int packed = 0;
 #pragma unroll
-    for (int r = 0; r < TH; ++r) {
-      const int y = y0 + r;
-      const bool row = part == 0 || (part == 1) == (r < TH / 2);
-      cd[r] = (x < nx && y < ny && row) ? code[(size_t)y * nx + x] : 0;
-    }
-#pragma unroll
-    for (int r = 0; r < TH; ++r) {
-      const bool f = cd[r] >= kSink;
-      const unsigned bal = __ballot_sync(0xffffffffu, f);
-      if (f) {
-        const int pos = n + __popc(bal & lt);
-        const int c = (y0 + r) * nx + x;
-        q.c[pos] = c;
-        q.pd[pos] = (unsigned)cd[r];
-        cp_async_elem(q.v + pos, h + c, true);
+    for (int i = 0; i < kWords; ++i) {
+      const int jw = lane + 32 * i, r = jw >> 3, xq = x0 + 4 * (jw & 7), y = y0 + r;
+      unsigned v = 0;
+      if (r >= rlo && r < rhi && y < ny && xq < nx) {
+        const uint8_t* p = code + (size_t)y * nx + xq;
+        if (xq + 3 < nx && ((size_t)p & 3) == 0) {
+          v = *reinterpret_cast<const unsigned*>(p);
+        } else {
+          for (int b = 0; b < 4 && xq + b < nx; ++b) v |= (unsigned)p[b] << (8 * b);
+        }
       }
-      n += __popc(bal);
+      roots[i] = v & 0x08080808u ? v : 0u;  // keep the codes of words with a root
+      packed |= __popc(v & 0x08080808u) << (10 * i);
+    }
+    int incl = packed;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - packed;
+#pragma unroll
+    for (int i = 0; i < kWords; ++i) {
+      const unsigned v = roots[i];
+      unsigned rb = v & 0x08080808u;
+      int pos = n + ((excl >> (10 * i)) & 1023);
+      const int jw = lane + 32 * i;
+      const int cw = (y0 + (jw >> 3)) * nx + x0 + 4 * (jw & 7);
+      while (rb) {
+        const int bit = __ffs(rb) - 1;  // 3, 11, 19 or 27
+        rb &= rb - 1;
+        const int c = cw + (bit >> 3);
+        q.c[pos] = c;
+        q.pd[pos] = (v >> (bit - 3)) & 0xFFu;
+        cp_async_elem(q.v + pos, h + c, true);
+        ++pos;
+      }
+      n += (tot >> (10 * i)) & 1023;
     }
   }
   if (lane == 0) {
@@ -212,14 +255,30 @@ __device__ __forceinline__ int tile_forest(const TileArgs<HT, kNewton>& a, const
   // entry, entries in queue order), so the queue stays in level order.  The
   // window that holds the first entry of level L ends level L+1's
   // predecessors: level L+1 starts after the donors of the entries before it.
+  // The next window's entries that already exist when a window starts (most
+  // of them: the queue usually runs a window ahead) have their cell and mask
+  // loaded then, so the mask load overlaps this window's work instead of
+  // heading the next window's dependency chain.  pre: entries below it were
+  // prefetched into (cn, mn) for the lane's entry of the coming window.
   int head = 0, tail = n, L = 1, B = n;  // B: first entry of level L
+  int cn = 0, mn = 0, pre = 0;
   while (head < tail) {
     const int w = min(32, tail - head);
     const int j = head + lane;
     int c = 0, msk = 0;
     if (lane < w) {
-      c = q.c[j];
-      msk = mask[c];
+      if (j < pre) {
+        c = cn;
+        msk = mn;
+      } else {
+        c = q.c[j];
+        msk = mask[c];
+      }
+    }
+    pre = tail;
+    if (j + w < tail) {
+      cn = q.c[j + w];
+      mn = mask[cn];
     }
     const int k = __popc(msk);
     int incl = k;
@@ -254,17 +313,12 @@ __device__ __forceinline__ int tile_forest(const TileArgs<HT, kNewton>& a, const
         const int v = __shfl_sync(0xffffffffu, incl, s + step - 1);
         if (v <= e) s += step;
       }
-      int pm = __shfl_sync(0xffffffffu, msk, s);
+      const int pm = __shfl_sync(0xffffffffu, msk, s);
       const int pc = __shfl_sync(0xffffffffu, c, s);
       const int pex = __shfl_sync(0xffffffffu, incl - k, s);
       if (e < tot) {
-        // drop the r = e - pex lowest set bits (pm has more than r set bits)
-        const int r = e - pex;
-        if (r > 0) pm &= pm - 1;
-        if (r > 1) pm &= pm - 1;
-        if (r > 2) pm &= pm - 1;
-        for (int t = 3; t < r; ++t) pm &= pm - 1;
-        const int kk = __ffs(pm) - 1;
+        // the (e - pex)-th set bit of the parent's mask (it has more bits)
+        const int kk = g_nth[pm * 8 + (e - pex)];
         const int pos = tail + e;
         const int cc = pc + off[kk];
         if (!in_bounds(a.st, pos, Q::kCap) || !in_bounds(a.st, cc, (long long)nx * ny)) continue;
@@ -379,6 +433,7 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   const TileQ<HT> q(dyn_smem + w * kWarpBytes);
   if (t < 8) s.off[t] = nbr_off(t, a.nx);
+  fill_nth(t, kBD);
   __syncthreads();
   TileArgs<HT, kNewton> ta;
   ta.nx = a.nx;
