@@ -340,10 +340,11 @@ __device__ __forceinline__ int receiver_f32_fast(const float hc, const float* v)
   const bool hasC = mC < hc, hasD = mD < hc;
   const int kC = v[1] == mC ? 1 : (v[3] == mC ? 3 : (v[4] == mC ? 4 : 6));
   const int kD = v[0] == mD ? 0 : (v[2] == mD ? 2 : (v[5] == mD ? 5 : 7));
-  const unsigned bmC = __float_as_uint(mC), bmD = __float_as_uint(mD);
-  const int ec = (int)(bc >> 23);
-  const bool okC = bmC != 0 && ec - max((int)(bmC >> 23), 1) <= 27;
-  const bool okD = bmD != 0 && ec - max((int)(bmD >> 23), 1) <= 27;
+  // a minimum m qualifies if m >= max(h_c 2^-27, 2^-126): then m is normal
+  // and at most 27 binades below h_c (h_c 2^-27 is exact whenever it is at
+  // least 2^-126), a subset of the exponent test of f32_group_safe
+  const float thr = fmaxf(__fmul_rn(hc, 0x1p-27f), 0x1p-126f);
+  const bool okC = mC >= thr, okD = mD >= thr;
   const float sC = __fsub_rn(hc, mC);
   const float sD = __fmul_rn(__fsub_rn(hc, mD), 0.70710677f);
   const bool cWins = sC > __fmul_rn(sD, 1.000003814697265625f);

@@ -64,6 +64,11 @@ __device__ __forceinline__ void fill_nth(int t, int nthreads) {
   }
 }
 
+// g_ptab[32 w + e]: warp w's start -> lane table of the current window of
+// Alg 3 (the lane whose donors start at position e of the window's donor
+// list), written and read between warp barriers.
+static __shared__ unsigned char g_ptab[32 * 32];
+
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -303,9 +308,36 @@ __device__ __forceinline__ int tile_forest(const TileArgs<HT, kNewton>& a, const
       B = tail + (before > 0 ? sb : 0);
       if (lane == 0) q.lev[L] = (unsigned short)B;
     }
-    // the window's tot donors, one per lane: donor e belongs to the first
-    // lane s whose inclusive count exceeds e, as its (e - excl(s))-th bit
-    for (int e0 = 0; e0 < tot; e0 += 32) {
+    // the window's tot donors, one per lane: donor e belongs to the lane s
+    // with excl(s) <= e < incl(s), as its (e - excl(s))-th set bit.  The
+    // first 32 (usually all of them): the lanes with donors are the ones
+    // whose start excl(s) is the largest start <= e, so a bitmap of the starts
+    // and a start -> lane table give s in a few instructions
+    if (tot > 0) {
+      unsigned char* const ptab = g_ptab + (threadIdx.x >> 5) * 32;
+      const int ex = incl - k;
+      const bool starts = k > 0 && ex < 32;
+      if (starts) ptab[ex] = (unsigned char)lane;
+      const unsigned sb = __reduce_or_sync(0xffffffffu, starts ? 1u << ex : 0u);
+      __syncwarp();
+      // bit 0 is set (the first lane with donors starts at 0), so p >= 0
+      const int p = 31 - __clz(sb & (0xFFFFFFFFu >> (31 - lane)));
+      const int s = ptab[p];
+      const int pm = __shfl_sync(0xffffffffu, msk, s);
+      const int pc = __shfl_sync(0xffffffffu, c, s);
+      if (lane < tot) {
+        const int kk = g_nth[pm * 8 + (lane - p)];
+        const int pos = tail + lane;
+        const int cc = pc + off[kk];
+        if (in_bounds(a.st, pos, Q::kCap) && in_bounds(a.st, cc, (long long)nx * ny)) {
+          q.c[pos] = cc;
+          q.pd[pos] = (1u << 16) | ((unsigned)(head + s) << 4) | (unsigned)(7 - kk);
+          cp_async_elem(q.v + pos, h + cc, true);
+        }
+      }
+    }
+    // donors 32 and up: s by a binary search over the inclusive counts
+    for (int e0 = 32; e0 < tot; e0 += 32) {
       const int e = e0 + lane;
       int s = 0;
 #pragma unroll
