@@ -875,6 +875,13 @@ __device__ __forceinline__ void codes_strip_f64(const double* S, uint8_t* code, 
 // (their decisions are independent, so the scheduler can interleave them);
 // the fast FP32 decision, and the exact one for the cells it leaves open
 // behind a warp-uniform branch (which also reports non-finite values).
+// Iterations whose two rows are both owned and neither is a perimeter row
+// (all but the first and the last one or two of a strip) run a form of the
+// body without the per-row tests of the others.
+template <bool B>
+struct RowKind {
+  static constexpr bool general = B;
+};
 __device__ __forceinline__ void codes_strip_f32(const float* S, uint8_t* code, uint8_t* mask,
                                                 int nx, int ny, int x, int y0, int y1, bool xin,
                                                 bool xperim, bool own, int sc, DevState* st) {
@@ -883,10 +890,12 @@ __device__ __forceinline__ void codes_strip_f32(const float* S, uint8_t* code, u
   float ul = el(0, sc - 1), uc = el(0, sc), ur = el(0, sc + 1);
   float ml = el(1, sc - 1), mc = el(1, sc), mr = el(1, sc + 1);
   long long at = (long long)(y0 - 1) * nx + x;
+  const long long N = (long long)nx * ny;
   unsigned pw = 0;
-  for (int y = y0 - 1; y <= y1; y += 2, at += 2 * (long long)nx) {
-    const bool two = y + 1 <= y1;  // the same for the whole warp
-    const int r = y + 1 - yb;      // staged row below row y
+  auto rows = [&](auto kind, int y) {
+    constexpr bool general = decltype(kind)::general;
+    const bool two = !general || y + 1 <= y1;  // the same for the whole warp
+    const int r = y + 1 - yb;                  // staged row below row y
     const int r2 = two ? r + 1 : r;
     const float dl = el(r, sc - 1), dc = el(r, sc), dr = el(r, sc + 1);
     const float fl = el(r2, sc - 1), fc = el(r2, sc), fr = el(r2, sc + 1);
@@ -894,31 +903,53 @@ __device__ __forceinline__ void codes_strip_f32(const float* S, uint8_t* code, u
     const float v1[8] = {ml, mc, mr, dl, dr, fl, fc, fr};
     int c0 = receiver_f32_fast(mc, v0);
     int c1 = receiver_f32_fast(dc, v1);
-    const bool in0 = xin && y >= 0 && y < ny;
-    const bool in1 = two && xin && y + 1 < ny;  // y + 1 >= 0 always
-    c0 = !in0 ? 0xFF : ((xperim || y == 0 || y == ny - 1) ? kEdge : c0);
-    c1 = !in1 ? 0xFF : ((xperim || y + 1 == 0 || y + 1 == ny - 1) ? kEdge : c1);
+    if constexpr (general) {
+      const bool in0 = xin && y >= 0 && y < ny;
+      const bool in1 = two && xin && y + 1 < ny;  // y + 1 >= 0 always
+      c0 = !in0 ? 0xFF : ((xperim || y == 0 || y == ny - 1) ? kEdge : c0);
+      c1 = !in1 ? 0xFF : ((xperim || y + 1 == 0 || y + 1 == ny - 1) ? kEdge : c1);
+    } else {
+      c0 = !xin ? 0xFF : (xperim ? kEdge : c0);
+      c1 = !xin ? 0xFF : (xperim ? kEdge : c1);
+    }
     if (__builtin_expect(__any_sync(0xffffffffu, c0 < 0 || c1 < 0), 0)) {
       if (c0 < 0) c0 = receiver_code_f32_vals(mc, v0, st);
       if (c1 < 0) c1 = receiver_code_f32_vals(dc, v1, st);
     }
-    const long long N = (long long)nx * ny;
-    if (own && in0 && y >= y0 && y < y1 && in_bounds(st, at, N)) code[at] = (uint8_t)c0;
-    if (own && in1 && y + 1 < y1 && in_bounds(st, at + nx, N)) code[at + nx] = (uint8_t)c1;
+    if constexpr (general) {
+      const bool in0 = xin && y >= 0 && y < ny;
+      const bool in1 = two && xin && y + 1 < ny;
+      if (own && in0 && y >= y0 && y < y1 && in_bounds(st, at, N)) code[at] = (uint8_t)c0;
+      if (own && in1 && y + 1 < y1 && in_bounds(st, at + nx, N)) code[at + nx] = (uint8_t)c1;
+    } else if (own) {
+      if (in_bounds(st, at, N)) code[at] = (uint8_t)c0;
+      if (in_bounds(st, at + nx, N)) code[at + nx] = (uint8_t)c1;
+    }
     pw = ((pw >> 8) & 0xFFFFu) | (pointer_bits(c0) << 16);
     unsigned pl = __shfl_up_sync(0xffffffffu, pw, 1);
     unsigned pr = __shfl_down_sync(0xffffffffu, pw, 1);
-    if (own && y > y0 && y <= y1 && in_bounds(st, at - nx, N))
-      mask[at - nx] = (uint8_t)mask_from_pointers(pl, pw, pr);
+    const int m0 = mask_from_pointers(pl, pw, pr);
+    if (own && (!general || (y > y0 && y <= y1)) && in_bounds(st, at - nx, N))
+      mask[at - nx] = (uint8_t)m0;
     if (two) {
       pw = ((pw >> 8) & 0xFFFFu) | (pointer_bits(c1) << 16);
       pl = __shfl_up_sync(0xffffffffu, pw, 1);
       pr = __shfl_down_sync(0xffffffffu, pw, 1);
-      if (own && y + 1 > y0 && in_bounds(st, at, N)) mask[at] = (uint8_t)mask_from_pointers(pl, pw, pr);
+      const int m1 = mask_from_pointers(pl, pw, pr);
+      if (own && (!general || y + 1 > y0) && in_bounds(st, at, N)) mask[at] = (uint8_t)m1;
     }
     ul = dl; uc = dc; ur = dr;
     ml = fl; mc = fc; mr = fr;
-  }
+  };
+  // rows y0 - 1 and y0 (row y0 - 1: codes for row y0's mask only)
+  int y = y0 - 1;
+  rows(RowKind<true>{}, y);
+  y += 2;
+  at += 2 * (long long)nx;
+  // rows y, y + 1 both owned (y + 1 < y1) and in [1, ny - 2]: y >= y0 + 1 >= 1
+  const int ylim = min(y1 - 1, ny - 2);
+  for (; y + 1 <= ylim; y += 2, at += 2 * (long long)nx) rows(RowKind<false>{}, y);
+  for (; y <= y1; y += 2, at += 2 * (long long)nx) rows(RowKind<true>{}, y);
 }
 
 template <typename HT>
