@@ -356,6 +356,34 @@ __device__ __forceinline__ int receiver_f32_fast(const float hc, const float* v)
   return undecided ? -1 : code;
 }
 
+// receiver_f32_fast for nine values that are all finite and non-negative
+// (the caller checks that separately, for a whole strip at a time): their
+// bit patterns order as the values do, so the group minima are unsigned
+// three-input minima and no per-cell range check is needed.  Returns the
+// same as receiver_f32_fast for such values.
+__device__ __forceinline__ int receiver_f32_fast_nn(const float hc, const float* v) {
+  const unsigned bc = __float_as_uint(hc);
+  const unsigned bC = __vimin3_u32(__float_as_uint(v[1]), __float_as_uint(v[3]),
+                                   min(__float_as_uint(v[4]), __float_as_uint(v[6])));
+  const unsigned bD = __vimin3_u32(__float_as_uint(v[0]), __float_as_uint(v[2]),
+                                   min(__float_as_uint(v[5]), __float_as_uint(v[7])));
+  const float mC = __uint_as_float(bC), mD = __uint_as_float(bD);
+  const bool hasC = bC < bc, hasD = bD < bc;
+  const int kC = v[1] == mC ? 1 : (v[3] == mC ? 3 : (v[4] == mC ? 4 : 6));
+  const int kD = v[0] == mD ? 0 : (v[2] == mD ? 2 : (v[5] == mD ? 5 : 7));
+  const float thr = fmaxf(__fmul_rn(hc, 0x1p-27f), 0x1p-126f);  // as in receiver_f32_fast
+  const bool okC = mC >= thr, okD = mD >= thr;
+  const float sC = __fsub_rn(hc, mC);
+  const float sD = __fmul_rn(__fsub_rn(hc, mD), 0.70710677f);
+  const bool cWins = sC > __fmul_rn(sD, 1.000003814697265625f);
+  const bool dWins = sD > __fmul_rn(sC, 1.000003814697265625f);
+  const bool both = hasC && hasD;
+  const bool undecided = (hasC && !okC) || (hasD && !okD) ||
+                         (both && (!(fminf(sC, sD) > 1e-30f) || (!cWins && !dWins)));
+  const int code = !hasC ? (hasD ? kD : kSink) : (!hasD ? kC : (cWins ? kC : kD));
+  return undecided ? -1 : code;
+}
+
 // st: where a non-finite value among the nine is reported (kErrInval); the
 // check runs only on the path that such values take (bit patterns at or
 // above that of +inf, which negative values share).
@@ -877,18 +905,26 @@ __device__ __forceinline__ void codes_strip_f64(const double* S, uint8_t* code, 
 // behind a warp-uniform branch (which also reports non-finite values).
 // Iterations whose two rows are both owned and neither is a perimeter row
 // (all but the first and the last one or two of a strip) run a form of the
-// body without the per-row tests of the others.
+// body without the per-row tests of the others.  The decisions assume
+// finite non-negative values (receiver_f32_fast_nn); every staged value a
+// lane reads goes into a running maximum of bit patterns, and a strip that
+// held a negative or non-finite value returns false: the caller then redoes
+// it with the per-cell checked form (which also reports non-finite values).
 template <bool B>
 struct RowKind {
   static constexpr bool general = B;
 };
-__device__ __forceinline__ void codes_strip_f32(const float* S, uint8_t* code, uint8_t* mask,
+__device__ __forceinline__ bool codes_strip_f32(const float* S, uint8_t* code, uint8_t* mask,
                                                 int nx, int ny, int x, int y0, int y1, bool xin,
                                                 bool xperim, bool own, int sc, DevState* st) {
   const int yb = y0 - 2;
   auto el = [&](int r, int col) -> float { return S[r * kStageCols + col]; };
+  auto bmax3 = [](float a, float b, float c) {
+    return __vimax3_u32(__float_as_uint(a), __float_as_uint(b), __float_as_uint(c));
+  };
   float ul = el(0, sc - 1), uc = el(0, sc), ur = el(0, sc + 1);
   float ml = el(1, sc - 1), mc = el(1, sc), mr = el(1, sc + 1);
+  unsigned worst = max(bmax3(ul, uc, ur), bmax3(ml, mc, mr));
   long long at = (long long)(y0 - 1) * nx + x;
   const long long N = (long long)nx * ny;
   unsigned pw = 0;
@@ -901,8 +937,9 @@ __device__ __forceinline__ void codes_strip_f32(const float* S, uint8_t* code, u
     const float fl = el(r2, sc - 1), fc = el(r2, sc), fr = el(r2, sc + 1);
     const float v0[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
     const float v1[8] = {ml, mc, mr, dl, dr, fl, fc, fr};
-    int c0 = receiver_f32_fast(mc, v0);
-    int c1 = receiver_f32_fast(dc, v1);
+    worst = __vimax3_u32(worst, bmax3(dl, dc, dr), bmax3(fl, fc, fr));
+    int c0 = receiver_f32_fast_nn(mc, v0);
+    int c1 = receiver_f32_fast_nn(dc, v1);
     if constexpr (general) {
       const bool in0 = xin && y >= 0 && y < ny;
       const bool in1 = two && xin && y + 1 < ny;  // y + 1 >= 0 always
@@ -950,6 +987,7 @@ __device__ __forceinline__ void codes_strip_f32(const float* S, uint8_t* code, u
   const int ylim = min(y1 - 1, ny - 2);
   for (; y + 1 <= ylim; y += 2, at += 2 * (long long)nx) rows(RowKind<false>{}, y);
   for (; y <= y1; y += 2, at += 2 * (long long)nx) rows(RowKind<true>{}, y);
+  return !__any_sync(0xffffffffu, worst >= Bits<float>::kInf);
 }
 
 template <typename HT>
@@ -969,11 +1007,11 @@ __device__ __forceinline__ void codes_strip(const HT* S, uint8_t* code, uint8_t*
       return;
     }
   } else {
-    if (!frozen) {
-      codes_strip_f32(reinterpret_cast<const float*>(S), code, mask, nx, ny, x, y0, y1, xin,
-                      xperim, own, sc, st);
+    // a strip holding a negative or non-finite value is redone below, cell by
+    // cell with the checked decision
+    if (!frozen && codes_strip_f32(reinterpret_cast<const float*>(S), code, mask, nx, ny, x, y0,
+                                   y1, xin, xperim, own, sc, st))
       return;
-    }
   }
   HT ul = HT(0), uc = HT(0), ur = HT(0), ml = HT(0), mc = HT(0), mr = HT(0);
   if (!frozen) {
