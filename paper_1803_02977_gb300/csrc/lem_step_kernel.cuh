@@ -357,30 +357,30 @@ __device__ __forceinline__ int receiver_f32_fast(const float hc, const float* v)
 }
 
 // receiver_f32_fast for nine values that are all finite and non-negative
-// (the caller checks that separately, for a whole strip at a time): their
-// bit patterns order as the values do, so the group minima are unsigned
-// three-input minima and no per-cell range check is needed.  Returns the
-// same as receiver_f32_fast for such values.
-__device__ __forceinline__ int receiver_f32_fast_nn(const float hc, const float* v) {
+// (the caller checks that separately, for a whole strip at a time), given
+// the bit patterns bC, bD of the cardinal and diagonal minima (for such
+// values bit patterns order as the values do).  Returns the same as
+// receiver_f32_fast for such values, or -1 (undecided) in more cases: a
+// minimum must be at least max(h_c 2^-27, 2^-76), which keeps both FP32
+// slopes of a two-group decision above 2^-99 (so above the 1e-30 floor of
+// receiver_f32_fast without testing it).
+__device__ __forceinline__ int receiver_f32_fast_nn(const float hc, const float* v, unsigned bC,
+                                                    unsigned bD) {
   const unsigned bc = __float_as_uint(hc);
-  const unsigned bC = __vimin3_u32(__float_as_uint(v[1]), __float_as_uint(v[3]),
-                                   min(__float_as_uint(v[4]), __float_as_uint(v[6])));
-  const unsigned bD = __vimin3_u32(__float_as_uint(v[0]), __float_as_uint(v[2]),
-                                   min(__float_as_uint(v[5]), __float_as_uint(v[7])));
   const float mC = __uint_as_float(bC), mD = __uint_as_float(bD);
   const bool hasC = bC < bc, hasD = bD < bc;
   const int kC = v[1] == mC ? 1 : (v[3] == mC ? 3 : (v[4] == mC ? 4 : 6));
   const int kD = v[0] == mD ? 0 : (v[2] == mD ? 2 : (v[5] == mD ? 5 : 7));
-  const float thr = fmaxf(__fmul_rn(hc, 0x1p-27f), 0x1p-126f);  // as in receiver_f32_fast
+  const float thr = fmaxf(__fmul_rn(hc, 0x1p-27f), 0x1p-76f);
   const bool okC = mC >= thr, okD = mD >= thr;
   const float sC = __fsub_rn(hc, mC);
   const float sD = __fmul_rn(__fsub_rn(hc, mD), 0.70710677f);
   const bool cWins = sC > __fmul_rn(sD, 1.000003814697265625f);
   const bool dWins = sD > __fmul_rn(sC, 1.000003814697265625f);
-  const bool both = hasC && hasD;
-  const bool undecided = (hasC && !okC) || (hasD && !okD) ||
-                         (both && (!(fminf(sC, sD) > 1e-30f) || (!cWins && !dWins)));
-  const int code = !hasC ? (hasD ? kD : kSink) : (!hasD ? kC : (cWins ? kC : kD));
+  const bool undecided =
+      (hasC && !okC) || (hasD && !okD) || (hasC && hasD && !cWins && !dWins);
+  const bool pickC = hasC && (!hasD || cWins);
+  const int code = pickC ? kC : (hasD ? kD : kSink);
   return undecided ? -1 : code;
 }
 
@@ -938,8 +938,16 @@ __device__ __forceinline__ bool codes_strip_f32(const float* S, uint8_t* code, u
     const float v0[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
     const float v1[8] = {ml, mc, mr, dl, dr, fl, fc, fr};
     worst = __vimax3_u32(worst, bmax3(dl, dc, dr), bmax3(fl, fc, fr));
-    int c0 = receiver_f32_fast_nn(mc, v0);
-    int c1 = receiver_f32_fast_nn(dc, v1);
+    // group minima of both cells: W-E of row y is diagonal to row y + 1, and
+    // SW-SE of row y is cardinal to it
+    const unsigned p1 = min(__float_as_uint(ml), __float_as_uint(mr));
+    const unsigned p2 = min(__float_as_uint(dl), __float_as_uint(dr));
+    const unsigned bC0 = __vimin3_u32(__float_as_uint(uc), __float_as_uint(dc), p1);
+    const unsigned bD0 = __vimin3_u32(__float_as_uint(ul), __float_as_uint(ur), p2);
+    const unsigned bC1 = __vimin3_u32(__float_as_uint(mc), __float_as_uint(fc), p2);
+    const unsigned bD1 = __vimin3_u32(__float_as_uint(fl), __float_as_uint(fr), p1);
+    int c0 = receiver_f32_fast_nn(mc, v0, bC0, bD0);
+    int c1 = receiver_f32_fast_nn(dc, v1, bC1, bD1);
     if constexpr (general) {
       const bool in0 = xin && y >= 0 && y < ny;
       const bool in1 = two && xin && y + 1 < ny;  // y + 1 >= 0 always
