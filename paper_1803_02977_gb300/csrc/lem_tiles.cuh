@@ -140,31 +140,41 @@ struct TileErode {
   const double2* Ftab;
   double dfac, dfacd, nexp, neps;
   int iters;
-  // Alg 5: h + dt*U (the same operations as uplift_sink)
+  // Alg 5: h + dt*U (the same operations as uplift_sink).  kField: U is the
+  // per-cell field Uf (else the scalar Udt); the caller picks the form once
+  // per forest, so the per-cell code carries no test of Uf.
+  template <bool kField>
   __device__ __forceinline__ HT uplift(int c, HT hcur) const {
     if constexpr (sizeof(HT) == 8) {
-      return __dadd_rn(hcur, Uf ? __dmul_rn(Uf[c], dt) : Udt);
+      return __dadd_rn(hcur, kField ? __dmul_rn(Uf[c], dt) : Udt);
     } else {
-      return __fadd_rn(hcur, Uf ? (float)__dmul_rn(Uf[c], dt) : Udt_f);
+      return __fadd_rn(hcur, kField ? (float)__dmul_rn(Uf[c], dt) : Udt_f);
     }
   }
-  __device__ __forceinline__ HT operator()(int c, int k, unsigned count, HT hcur, HT hr) const {
+  template <bool kField>
+  __device__ __forceinline__ HT erode(int c, int k, unsigned count, HT hcur, HT hr) const {
     const int i = (nbr_diag(k) ? tn : 0) + (int)count;
     if constexpr (kNewton) {
       // the operations of erode_newton for a tabulated count
-      const double h0 = (double)hcur + (Uf ? __dmul_rn(Uf[c], dt) : Udt);
+      const double h0 = (double)hcur + (kField ? __dmul_rn(Uf[c], dt) : Udt);
       const double F = Ftab[i].x * (nbr_diag(k) ? dfacd : dfac);
       return (HT)newton_solve(h0, (double)hr, F, nexp, neps, iters);
     } else if constexpr (sizeof(HT) == 8) {
       const double g = static_cast<const double2*>(gtab)[i].y;
-      const double h0 = __dadd_rn(hcur, Uf ? __dmul_rn(Uf[c], dt) : Udt);
+      const double h0 = __dadd_rn(hcur, kField ? __dmul_rn(Uf[c], dt) : Udt);
       return __fma_rn(-g, __dsub_rn(h0, hr), h0);
     } else {
       const float g = static_cast<const float*>(gtab)[i];
-      const float h0 = __fadd_rn(hcur, Uf ? (float)__dmul_rn(Uf[c], dt) : Udt_f);
+      const float h0 = __fadd_rn(hcur, kField ? (float)__dmul_rn(Uf[c], dt) : Udt_f);
       return __fmaf_rn(-g, __fsub_rn(h0, hr), h0);
     }
   }
+};
+
+// A compile-time flag passed as a value (for generic lambdas).
+template <bool B>
+struct Flag {
+  static constexpr bool value = B;
 };
 
 // What a warp forest reads: the grid, its codes and masks (Algs 1-2 done),
@@ -378,27 +388,36 @@ __device__ __forceinline__ int tile_forest(const TileArgs<HT, kNewton>& a, const
   __syncwarp();
   const TileErode<HT, kNewton> ero = a.ero;
   HT* const hh = a.h;
-  // Alg 5 on level 0: pits are uplifted, the perimeter stays
-  for (int jj = lane; jj < n; jj += 32) {
-    if ((q.pd[jj] & 15u) == (unsigned)kSink) {
-      const int c = q.c[jj];
-      const HT hc = ero.uplift(c, q.v[jj]);
-      hh[c] = hc;
-      q.v[jj] = hc;
-    }
-  }
-  __syncwarp();
-  // Alg 6 from level 1 up: the receiver's new elevation is the parent's v
-  for (int l = 1; l < L; ++l) {
-    const int l0 = q.lev[l], l1 = q.lev[l + 1];
-    for (int jj = l0 + lane; jj < l1; jj += 32) {
-      const int c = q.c[jj];
-      const unsigned pd = q.pd[jj];
-      const HT hn = ero(c, (int)(pd & 15u), pd >> 16, q.v[jj], q.v[(pd >> 4) & 0xFFFu]);
-      if (in_bounds(a.st, c, (long long)nx * ny)) hh[c] = hn;
-      q.v[jj] = hn;
+  auto erode_levels = [&](auto field) {
+    constexpr bool kField = decltype(field)::value;
+    // Alg 5 on level 0: pits are uplifted, the perimeter stays
+    for (int jj = lane; jj < n; jj += 32) {
+      if ((q.pd[jj] & 15u) == (unsigned)kSink) {
+        const int c = q.c[jj];
+        const HT hc = ero.template uplift<kField>(c, q.v[jj]);
+        hh[c] = hc;
+        q.v[jj] = hc;
+      }
     }
     __syncwarp();
+    // Alg 6 from level 1 up: the receiver's new elevation is the parent's v
+    for (int l = 1; l < L; ++l) {
+      const int l0 = q.lev[l], l1 = q.lev[l + 1];
+      for (int jj = l0 + lane; jj < l1; jj += 32) {
+        const int c = q.c[jj];
+        const unsigned pd = q.pd[jj];
+        const HT hn = ero.template erode<kField>(c, (int)(pd & 15u), pd >> 16, q.v[jj],
+                                                 q.v[(pd >> 4) & 0xFFFu]);
+        if (in_bounds(a.st, c, (long long)nx * ny)) hh[c] = hn;
+        q.v[jj] = hn;
+      }
+      __syncwarp();
+    }
+  };
+  if (ero.Uf != nullptr) {
+    erode_levels(Flag<true>{});
+  } else {
+    erode_levels(Flag<false>{});
   }
   return tail;
 }
