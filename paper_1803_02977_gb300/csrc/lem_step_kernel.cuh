@@ -240,6 +240,33 @@ __device__ __forceinline__ int receiver_code_hi_words(const unsigned hc, const u
   return undecided ? -1 : code;
 }
 
+// receiver_code_hi_words for nine high words of finite non-negative values
+// (the caller checks that for a whole strip at a time), given each group's
+// smallest (mC, mD) and second smallest (rC, rD, counting repeats) high word:
+// the minimum is unique and no member holds the next high word exactly when
+// the second smallest is at least two above it.  The same result as
+// receiver_code_hi_words for such values.
+__device__ __forceinline__ int receiver_code_hi_nn(const unsigned hc, const unsigned* x,
+                                                   unsigned mC, unsigned rC, unsigned mD,
+                                                   unsigned rD) {
+  const bool hasC = mC < hc, hasD = mD < hc;
+  const bool badC = rC < mC + 2u || (hc >> 20) - (mC >> 20) > 18u;
+  const bool badD = rD < mD + 2u || (hc >> 20) - (mD >> 20) > 18u;
+  const int kC = x[1] == mC ? 1 : (x[3] == mC ? 3 : (x[4] == mC ? 4 : 6));
+  const int kD = x[0] == mD ? 0 : (x[2] == mD ? 2 : (x[5] == mD ? 5 : 7));
+  // slopes in FP32 from the high words, as in receiver_code_hi_words
+  const float fc = __uint_as_float((hc - (896u << 20)) << 3);
+  const float sC = __fsub_rn(fc, __uint_as_float((mC - (896u << 20)) << 3));
+  const float sD = __fmul_rn(__fsub_rn(fc, __uint_as_float((mD - (896u << 20)) << 3)), 0.70710677f);
+  const float tol = __fmul_rn(__fadd_rn(fc, fmaxf(sC, sD)), 1.52587890625e-05f);  // 2^-16
+  const bool cWins = __fsub_rn(sC, sD) > tol, dWins = __fsub_rn(sD, sC) > tol;
+  const bool undecided = hc < (915u << 20) || hc >= (1151u << 20) || mC == hc || mD == hc ||
+                         (hasC && badC) || (hasD && badD) || (hasC && hasD && !cWins && !dWins);
+  const bool pickC = hasC && (!hasD || cWins);
+  const int code = pickC ? kC : (hasD ? kD : kSink);
+  return undecided ? -1 : code;
+}
+
 __device__ __forceinline__ int receiver_code_hi(const double hcd, const double* v) {
   unsigned x[8];
 #pragma unroll
@@ -830,10 +857,28 @@ __device__ __forceinline__ int mask_from_pointers(unsigned pl, unsigned pw, unsi
 // words of the values (receiver_code_hi_words decides from them alone); a
 // cell it leaves undecided reloads its nine doubles from the staged strip
 // for the exact comparison.
+template <bool B>
+struct RowKind {
+  static constexpr bool general = B;
+};
+// A compile-time flag passed as a value (for generic lambdas).
+template <bool B>
+struct Flag {
+  static constexpr bool value = B;
+};
+// Smallest and second smallest (counting repeats) of two sorted pairs.
+struct Low2 {
+  unsigned lo, hi;
+};
+__device__ __forceinline__ Low2 low2(unsigned a, unsigned b) { return Low2{min(a, b), max(a, b)}; }
+__device__ __forceinline__ Low2 low2(Low2 p, Low2 q) {
+  return Low2{min(p.lo, q.lo), __vimin3_u32(max(p.lo, q.lo), p.hi, q.hi)};
+}
 __device__ __forceinline__ void codes_strip_f64(const double* S, uint8_t* code, uint8_t* mask,
                                                 int nx, int ny, int x, int y0, int y1, bool xin,
                                                 bool xperim, bool own, int sc, DevState* st) {
   const int yb = y0 - 2;
+  const long long N = (long long)nx * ny;
   // high word of staged element (row r, column col)
   auto hw = [&](int r, int col) -> unsigned {
     return reinterpret_cast<const unsigned*>(S + r * kStageCols + col)[1];
@@ -854,49 +899,92 @@ __device__ __forceinline__ void codes_strip_f64(const double* S, uint8_t* code, 
     }
     return receiver_code_vals(md[0], v);
   };
-  unsigned ul = hw(0, sc - 1), uc = hw(0, sc), ur = hw(0, sc + 1);
-  unsigned ml = hw(1, sc - 1), mc = hw(1, sc), mr = hw(1, sc + 1);
-  long long at = (long long)(y0 - 1) * nx + x;
-  unsigned pw = 0;
-  // two rows per iteration (y and y + 1): their receiver decisions are
-  // independent, so the scheduler can interleave them
-  for (int y = y0 - 1; y <= y1; y += 2, at += 2 * (long long)nx) {
-    const bool two = y + 1 <= y1;  // the same for the whole warp
-    const int r = y + 1 - yb;      // staged row below row y
-    const int r2 = two ? r + 1 : r;
-    const unsigned dl = hw(r, sc - 1), dc = hw(r, sc), dr = hw(r, sc + 1);
-    const unsigned el = hw(r2, sc - 1), ec = hw(r2, sc), er = hw(r2, sc + 1);
-    const unsigned xs0[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
-    const unsigned xs1[8] = {ml, mc, mr, dl, dr, el, ec, er};
-    int c0 = receiver_code_hi_words(mc, xs0);
-    int c1 = receiver_code_hi_words(dc, xs1);
-    const bool in0 = xin && y >= 0 && y < ny;
-    const bool in1 = two && xin && y + 1 < ny;  // y + 1 >= 0 always
-    c0 = !in0 ? 0xFF : ((xperim || y == 0 || y == ny - 1) ? kEdge : c0);
-    c1 = !in1 ? 0xFF : ((xperim || y + 1 == 0 || y + 1 == ny - 1) ? kEdge : c1);
-    // cells the high words leave open take the exact comparison, behind a
-    // warp-uniform branch so that the other cells do not execute it
-    if (__builtin_expect(__any_sync(0xffffffffu, c0 < 0 || c1 < 0), 0)) {
-      if (c0 < 0) c0 = exact(r);
-      if (c1 < 0) c1 = exact(r2);
-    }
-    const long long N = (long long)nx * ny;
-    if (own && in0 && y >= y0 && y < y1 && in_bounds(st, at, N)) code[at] = (uint8_t)c0;
-    if (own && in1 && y + 1 < y1 && in_bounds(st, at + nx, N)) code[at + nx] = (uint8_t)c1;
-    pw = ((pw >> 8) & 0xFFFFu) | (pointer_bits(c0) << 16);
-    unsigned pl = __shfl_up_sync(0xffffffffu, pw, 1);
-    unsigned pr = __shfl_down_sync(0xffffffffu, pw, 1);
-    if (own && y > y0 && y <= y1 && in_bounds(st, at - nx, N))
-      mask[at - nx] = (uint8_t)mask_from_pointers(pl, pw, pr);
-    if (two) {
-      pw = ((pw >> 8) & 0xFFFFu) | (pointer_bits(c1) << 16);
-      pl = __shfl_up_sync(0xffffffffu, pw, 1);
-      pr = __shfl_down_sync(0xffffffffu, pw, 1);
-      if (own && y + 1 > y0 && in_bounds(st, at, N)) mask[at] = (uint8_t)mask_from_pointers(pl, pw, pr);
-    }
-    ul = dl; uc = dc; ur = dr;
-    ml = el; mc = ec; mr = er;
-  }
+  // one pass over the strip: high-word decisions (a running maximum of every
+  // high word read is returned), or with kExact every interior cell exact
+  auto pass = [&](auto exact_kind) -> unsigned {
+    constexpr bool kExact = decltype(exact_kind)::value;
+    unsigned ul = hw(0, sc - 1), uc = hw(0, sc), ur = hw(0, sc + 1);
+    unsigned ml = hw(1, sc - 1), mc = hw(1, sc), mr = hw(1, sc + 1);
+    unsigned worst = max(__vimax3_u32(ul, uc, ur), __vimax3_u32(ml, mc, mr));
+    long long at = (long long)(y0 - 1) * nx + x;
+    unsigned pw = 0;
+    // two rows per iteration (y and y + 1): their receiver decisions are
+    // independent, so the scheduler can interleave them; iterations whose
+    // rows are both owned interior rows skip the per-row tests
+    auto rows = [&](auto kind, int y) {
+      constexpr bool general = decltype(kind)::general;
+      const bool two = !general || y + 1 <= y1;  // the same for the whole warp
+      const int r = y + 1 - yb;                  // staged row below row y
+      const int r2 = two ? r + 1 : r;
+      const unsigned dl = hw(r, sc - 1), dc = hw(r, sc), dr = hw(r, sc + 1);
+      const unsigned el = hw(r2, sc - 1), ec = hw(r2, sc), er = hw(r2, sc + 1);
+      worst = __vimax3_u32(worst, __vimax3_u32(dl, dc, dr), __vimax3_u32(el, ec, er));
+      bool in0 = xin, in1 = xin, edge0 = xperim, edge1 = xperim;
+      if constexpr (general) {
+        in0 = xin && y >= 0 && y < ny;
+        in1 = two && xin && y + 1 < ny;  // y + 1 >= 0 always
+        edge0 = xperim || y == 0 || y == ny - 1;
+        edge1 = xperim || y + 1 == 0 || y + 1 == ny - 1;
+      }
+      int c0, c1;
+      if constexpr (kExact) {
+        c0 = !in0 ? 0xFF : (edge0 ? kEdge : exact(r));
+        c1 = !in1 ? 0xFF : (edge1 ? kEdge : exact(r2));
+      } else {
+        // group minima and runners-up: W-E of row y is diagonal to row
+        // y + 1, and SW-SE of row y is cardinal to it
+        const Low2 pWE = low2(ml, mr), pS = low2(dl, dr);
+        const Low2 gC0 = low2(pWE, low2(uc, dc)), gD0 = low2(low2(ul, ur), pS);
+        const Low2 gC1 = low2(pS, low2(mc, ec)), gD1 = low2(pWE, low2(el, er));
+        const unsigned xs0[8] = {ul, uc, ur, ml, mr, dl, dc, dr};
+        const unsigned xs1[8] = {ml, mc, mr, dl, dr, el, ec, er};
+        c0 = receiver_code_hi_nn(mc, xs0, gC0.lo, gC0.hi, gD0.lo, gD0.hi);
+        c1 = receiver_code_hi_nn(dc, xs1, gC1.lo, gC1.hi, gD1.lo, gD1.hi);
+        c0 = !in0 ? 0xFF : (edge0 ? kEdge : c0);
+        c1 = !in1 ? 0xFF : (edge1 ? kEdge : c1);
+        // cells the high words leave open take the exact comparison, behind
+        // a warp-uniform branch so that the other cells do not execute it
+        if (__builtin_expect(__any_sync(0xffffffffu, c0 < 0 || c1 < 0), 0)) {
+          if (c0 < 0) c0 = exact(r);
+          if (c1 < 0) c1 = exact(r2);
+        }
+      }
+      if constexpr (general) {
+        if (own && in0 && y >= y0 && y < y1 && in_bounds(st, at, N)) code[at] = (uint8_t)c0;
+        if (own && in1 && y + 1 < y1 && in_bounds(st, at + nx, N)) code[at + nx] = (uint8_t)c1;
+      } else if (own) {
+        if (in_bounds(st, at, N)) code[at] = (uint8_t)c0;
+        if (in_bounds(st, at + nx, N)) code[at + nx] = (uint8_t)c1;
+      }
+      pw = ((pw >> 8) & 0xFFFFu) | (pointer_bits(c0) << 16);
+      unsigned pl = __shfl_up_sync(0xffffffffu, pw, 1);
+      unsigned pr = __shfl_down_sync(0xffffffffu, pw, 1);
+      const int m0 = mask_from_pointers(pl, pw, pr);
+      if (own && (!general || (y > y0 && y <= y1)) && in_bounds(st, at - nx, N))
+        mask[at - nx] = (uint8_t)m0;
+      if (two) {
+        pw = ((pw >> 8) & 0xFFFFu) | (pointer_bits(c1) << 16);
+        pl = __shfl_up_sync(0xffffffffu, pw, 1);
+        pr = __shfl_down_sync(0xffffffffu, pw, 1);
+        const int m1 = mask_from_pointers(pl, pw, pr);
+        if (own && (!general || y + 1 > y0) && in_bounds(st, at, N)) mask[at] = (uint8_t)m1;
+      }
+      ul = dl; uc = dc; ur = dr;
+      ml = el; mc = ec; mr = er;
+    };
+    int y = y0 - 1;
+    rows(RowKind<true>{}, y);
+    y += 2;
+    at += 2 * (long long)nx;
+    const int ylim = min(y1 - 1, ny - 2);
+    for (; y + 1 <= ylim; y += 2, at += 2 * (long long)nx) rows(RowKind<false>{}, y);
+    for (; y <= y1; y += 2, at += 2 * (long long)nx) rows(RowKind<true>{}, y);
+    return worst;
+  };
+  // a strip that held a negative or non-finite value (a high word at or
+  // above that of +inf) is redone with every interior cell exact, which
+  // also reports non-finite values
+  if (__any_sync(0xffffffffu, pass(Flag<false>{}) >= 0x7FF00000u)) pass(Flag<true>{});
 }
 
 // codes_strip for FP32 elevations: two rows per iteration, as the FP64 form
@@ -910,10 +998,6 @@ __device__ __forceinline__ void codes_strip_f64(const double* S, uint8_t* code, 
 // lane reads goes into a running maximum of bit patterns, and a strip that
 // held a negative or non-finite value returns false: the caller then redoes
 // it with the per-cell checked form (which also reports non-finite values).
-template <bool B>
-struct RowKind {
-  static constexpr bool general = B;
-};
 __device__ __forceinline__ bool codes_strip_f32(const float* S, uint8_t* code, uint8_t* mask,
                                                 int nx, int ny, int x, int y0, int y1, bool xin,
                                                 bool xperim, bool own, int sc, DevState* st) {

@@ -171,11 +171,6 @@ struct TileErode {
   }
 };
 
-// A compile-time flag passed as a value (for generic lambdas).
-template <bool B>
-struct Flag {
-  static constexpr bool value = B;
-};
 
 // What a warp forest reads: the grid, its codes and masks (Algs 1-2 done),
 // the elevations it erodes and the erosion parameters.
