@@ -65,6 +65,11 @@ CASES = [
     ("tilted_1500x64", lambda: _tilted(1500, 64, 7, slope=0.2)),
     ("1031x777_int", lambda: _int_grid(1031, 777, 8, levels=40)),
     ("far_minima_300x200", lambda: _far_minima(300, 200, 31)),
+    # negative elevations (a surface below a datum): the codes pass redoes
+    # every strip holding one with the exact per-cell form
+    ("negative_157x212", lambda: np.random.default_rng(8).random((157, 212)) - 0.5),
+    ("below_datum_300x200", lambda: _tilted(300, 200, 6) - 50.0),
+    ("signed_zeros_90x70", lambda: _signed_zeros(90, 70, 12)),
 ]
 
 
@@ -103,6 +108,15 @@ def test_stages_fp64_bit_exact_and_tolerance(name, make):
     want, _ = oracle.step(h0, p)
     scale = max(np.abs(want).max(), 1.0)
     assert np.abs(g["h"] - want).max() <= REL64 * scale
+
+
+def _signed_zeros(nx, ny, seed):
+    """Zeros of both signs among small positive values: -0.0 has the sign bit
+    set, so a strip holding one takes the codes pass's checked form."""
+    rng = np.random.default_rng(seed)
+    h = rng.choice([0.0, -0.0, 0.25, 0.5, 1.0], (ny, nx))
+    h[1::5, 2::7] = 3.0
+    return h
 
 
 def _adversarial(kind, nx, ny, seed):
@@ -184,6 +198,8 @@ FP32_STEP_CASES = [
     ("mixed_zeros", lambda: _adversarial("mixed_zeros", 211, 157, 7)),
     ("low_bits", lambda: _adversarial("low_bits", 211, 157, 7)),
     ("negative", lambda: np.random.default_rng(8).random((157, 212)) - 0.5),
+    ("below_datum_300x200", lambda: _tilted(300, 200, 6) - 50.0),
+    ("signed_zeros_90x70", lambda: _signed_zeros(90, 70, 12)),
     ("grid2048_f32", lambda: synth.workload("grid2048_f32").initial()),
 ]
 
