@@ -105,6 +105,9 @@ __global__ void __launch_bounds__(BD) lem_batch_kernel(BatchArgs a) {
     g.pqf = a.pqf + o;
     g.cntq = a.cntq + o;
     g.plev = a.plev + o + r;
+    // the warp slices are idle while the block forest runs
+    g.splev = reinterpret_cast<int*>(dyn_smem);
+    g.splev_cap = (BD / 32) * kWarpBytes / (int)sizeof(int);
     g.Udt = a.Udt[r];
     const float* tab = a.gtab + (size_t)r * 2 * kBatchTN;
     ErosionFactors ef;

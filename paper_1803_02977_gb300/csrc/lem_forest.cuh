@@ -6,8 +6,13 @@
 // The queue lives in global memory in breadth-first order: level 0 (the
 // trees' roots, given) first, then each level's donors in the order of their
 // receivers, each entry with its donor mask (pqm), receiver code (pqk) and
-// the position of its first donor (pqf).  Accumulation then runs in queue
-// order on a queue-ordered count array; erosion gathers elevations.
+// the queue position of its receiver (pqf, levels >= 1).  Accumulation runs
+// on a queue-ordered count array, each entry adding its final count to its
+// receiver's (deepest level first); erosion gathers elevations.  A deep
+// forest is latency-bound, level by level, so each level reads as little as
+// it can after the previous one: the level offsets are mirrored in shared
+// memory (splev, the block's warp slices, idle by then), and a count push
+// needs only the entry's own words.
 #pragma once
 
 #include "lem_step_kernel.cuh"
@@ -34,7 +39,14 @@ struct ForestGrid {
   int* pqf;
   int* cntq;
   int* plev;       // level offsets, capacity N + 1
+  int* splev;      // their first splev_cap entries, mirrored in shared memory
+  int splev_cap;
   float Udt;       // U*dt, rounded once to float
+  __device__ __forceinline__ void set_level(int l, int v) const {
+    plev[l] = v;
+    if (l < splev_cap) splev[l] = v;
+  }
+  __device__ __forceinline__ int level(int l) const { return l < splev_cap ? splev[l] : plev[l]; }
 };
 
 // Alg 3: expand levels from level 0 = [0, n0) (pq with pqm and pqk filled).  Entries of a round are taken
@@ -49,8 +61,8 @@ __device__ int forest_levels(const ForestGrid& g, int n0, ForestSmem<BD, PI>& s)
   const int nx = g.nx;
   int lo = 0, hi = n0, PL = 1;
   if (t == 0) {
-    g.plev[0] = 0;
-    g.plev[1] = n0;
+    g.set_level(0, 0);
+    g.set_level(1, n0);
   }
   while (lo < hi) {
     int run = hi;
@@ -116,13 +128,15 @@ __device__ int forest_levels(const ForestGrid& g, int n0, ForestSmem<BD, PI>& s)
 #pragma unroll
       for (int i = 0; i < PI; ++i) {
         int pos = pos_i[i];
-        if (cs[i] >= 0) g.pqf[base + i * BD + t] = pos;
+        const int parent = base + i * BD + t;
         int msk = ms[i];
         while (msk) {
           const int k = __ffs(msk) - 1;
           msk &= msk - 1;
           g.pq[pos] = cs[i] + nbr_off(k, nx);
           g.pqk[pos] = (uint8_t)(7 - k);
+          g.pqf[pos] = parent;
+          g.cntq[pos] = 1;
           ++pos;
         }
       }
@@ -131,7 +145,7 @@ __device__ int forest_levels(const ForestGrid& g, int n0, ForestSmem<BD, PI>& s)
     __syncthreads();
     if (run == hi) break;
     ++PL;
-    if (t == 0) g.plev[PL] = run;
+    if (t == 0) g.set_level(PL, run);
     lo = hi;
     hi = run;
   }
@@ -139,19 +153,15 @@ __device__ int forest_levels(const ForestGrid& g, int n0, ForestSmem<BD, PI>& s)
   return PL;
 }
 
-// Alg 4 in queue order, levels PL-1 down to 1: 1 + the counts of the donors
-// at [pqf, pqf + popc(pqm)).
+// Alg 4, levels PL-1 down to 2: every entry adds its count (1 when it was
+// queued, final once its own level comes up) to its receiver's entry; level
+// 1 feeds only level 0, which does not erode.
 template <int BD>
 __device__ void forest_accumulate(const ForestGrid& g, int PL) {
   const int t = threadIdx.x;
-  for (int l = PL - 1; l >= 1; --l) {
-    const int l0 = g.plev[l], l1 = g.plev[l + 1];
-    for (int j = l0 + t; j < l1; j += BD) {
-      const int f = g.pqf[j], n = __popc(g.pqm[j]);
-      int sum = 1;
-      for (int q = 0; q < n; ++q) sum += g.cntq[f + q];
-      g.cntq[j] = sum;
-    }
+  for (int l = PL - 1; l >= 2; --l) {
+    const int l0 = g.level(l), l1 = g.level(l + 1);
+    for (int j = l0 + t; j < l1; j += BD) atomicAdd(g.cntq + g.pqf[j], g.cntq[j]);
     __syncthreads();
   }
 }
@@ -182,7 +192,7 @@ __device__ void forest_erode(const ForestGrid& g, int PL, const ErosionFactors& 
     }
   __syncthreads();
   for (int l = 1; l < PL; ++l) {
-    const int l0 = g.plev[l], l1 = g.plev[l + 1];
+    const int l0 = g.level(l), l1 = g.level(l + 1);
     for (int j = l0 + t; j < l1; j += BD) {
       const int c = g.pq[j], k = g.pqk[j];
       const float gk = ef(g.cntq[j], nbr_diag(k));

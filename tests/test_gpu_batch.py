@@ -50,6 +50,40 @@ def _singles(surfaces, Ks, ms, steps):
     return out
 
 
+def _ramp(nx, ny, seed):
+    # a plane falling toward the west edge plus small noise: trees as long as
+    # the grid is wide, hundreds of levels, all in the block-wide forest
+    x = np.arange(nx, dtype=np.float64)[None, :]
+    h = 5.0 * x + 0.01 * synth.uniform01(seed, nx * ny).reshape(ny, nx)
+    h[0, :] = h[-1, :] = h[:, 0] = h[:, -1] = 0.0
+    return h
+
+
+@pytest.mark.parametrize("shape", [(256, 4), (1024, 8)])
+def test_batch_deep_forests_against_oracle(shape):
+    """Trees hundreds of levels deep (the block-wide forest: level offsets in
+    shared memory, counts pushed to the receivers) per step against the
+    oracle, with shallow realizations beside them."""
+    from paper_1803_02977_gb300 import lem
+    surfaces = [_ramp(700, 40, 21), _funnel(97, 83, 1002, cx=40, cy=41, r=16.0),
+                synth.noise_surface(129, 65, 5), _ramp(310, 300, 22)]
+    Ks, ms = [2e-5, 1e-5, 3e-5, 1e-6], [0.5, 0.45, 0.55, 0.6]
+    b = lem.Batch(surfaces, dx=100.0, K=Ks, m=ms, U=1e-3, dt=1000.0)
+    b.set_config(*shape)
+    for _ in range(2):
+        before = [b.surface(r).cpu().numpy().astype(np.float64) for r in range(b.R)]
+        b.step(1)
+        b.sync()
+        for r in range(b.R):
+            want, g = oracle.step(before[r], oracle.params(K=Ks[r], m=ms[r]))
+            if r in (0, 3):
+                assert g.levels.size - 1 > 250  # deep: far beyond a warp's 127 levels
+            got = b.surface(r).cpu().numpy().astype(np.float64)
+            tol = 4 * 2.0 ** -24 * np.maximum(np.abs(want), 1.0)
+            assert np.all(np.abs(got - want) <= tol), f"realization {r}"
+    b.close()
+
+
 @pytest.mark.parametrize("shape", [(256, 4), (256, 8), (512, 4), (512, 8), (1024, 4), (1024, 8)])
 def test_batch_equals_single_grid_path(shape):
     from paper_1803_02977_gb300 import lem
