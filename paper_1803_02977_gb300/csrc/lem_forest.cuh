@@ -49,16 +49,101 @@ struct ForestGrid {
   __device__ __forceinline__ int level(int l) const { return l < splev_cap ? splev[l] : plev[l]; }
 };
 
-// Alg 3: expand levels from level 0 = [0, n0) (pq with pqm and pqk filled).  Entries of a round are taken
-// PI per thread (strided, so the loads coalesce) and emitted in parent order.
-// Returns the number of levels PL; plev[0..PL] holds the offsets.
-template <int BD, int PI>
-__device__ int forest_levels(const ForestGrid& g, int n0, ForestSmem<BD, PI>& s) {
+// One round of Alg 3: the entries [base, base + PIR * BD) of the level
+// [lo, hi), PIR per thread (strided, so the loads coalesce), emit their
+// donors at run.. in parent order.  Returns the number emitted.
+template <int BD, int PI, int PIR>
+__device__ __forceinline__ int forest_round(const ForestGrid& g, ForestSmem<BD, PI>& s, int lo,
+                                            int hi, int base, int run) {
   constexpr int W = BD / 32;
-  constexpr int C = PI * W;          // chunk totals per round
+  constexpr int C = PIR * W;          // chunk totals of the round
   constexpr int PER = (C + 31) / 32;  // chunk totals per lane of warp 0
+  static_assert(PIR <= PI, "chunk totals fit");
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const int nx = g.nx;
+  int cs[PIR], ms[PIR];
+#pragma unroll
+  for (int i = 0; i < PIR; ++i) {
+    const int j = base + i * BD + t;
+    cs[i] = (j < hi) ? g.pq[j] : -1;
+  }
+  if (lo == 0) {
+#pragma unroll
+    for (int i = 0; i < PIR; ++i) ms[i] = (cs[i] >= 0) ? g.pqm[base + i * BD + t] : 0;
+  } else {
+#pragma unroll
+    for (int i = 0; i < PIR; ++i) ms[i] = (cs[i] >= 0) ? g.mask[cs[i]] : 0;
+#pragma unroll
+    for (int i = 0; i < PIR; ++i)
+      if (cs[i] >= 0) g.pqm[base + i * BD + t] = (uint8_t)ms[i];
+  }
+  int pos_i[PIR];
+#pragma unroll
+  for (int i = 0; i < PIR; ++i) {
+    const int cnt = __popc(ms[i]);
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    pos_i[i] = x - cnt;
+    if (lane == 31) s.chunk[i * W + w] = x;
+  }
+  __syncthreads();
+  if (w == 0) {
+    int v[PER], sum = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = lane * PER + q;
+      v[q] = (idx < C) ? s.chunk[idx] : 0;
+      sum += v[q];
+    }
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s.chunk_total = x;
+    int acc = x - sum;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = lane * PER + q;
+      if (idx < C) s.chunk[idx] = acc;
+      acc += v[q];
+    }
+  }
+  __syncthreads();
+  const int tot = s.chunk_total;
+#pragma unroll
+  for (int i = 0; i < PIR; ++i) pos_i[i] += run + s.chunk[i * W + w];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < PIR; ++i) {
+    int pos = pos_i[i];
+    const int parent = base + i * BD + t;
+    int msk = ms[i];
+    while (msk) {
+      const int k = __ffs(msk) - 1;
+      msk &= msk - 1;
+      g.pq[pos] = cs[i] + nbr_off(k, nx);
+      g.pqk[pos] = (uint8_t)(7 - k);
+      g.pqf[pos] = parent;
+      g.cntq[pos] = 1;
+      ++pos;
+    }
+  }
+  return tot;
+}
+
+// Alg 3: expand levels from level 0 = [0, n0) (pq with pqm and pqk filled).
+// A level of at most BD entries (deep trees are mostly such levels) takes one
+// round of one entry per thread; wider ones rounds of PI per thread.
+// Returns the number of levels PL; the level offsets go to plev (and splev).
+template <int BD, int PI>
+__device__ int forest_levels(const ForestGrid& g, int n0, ForestSmem<BD, PI>& s) {
+  const int t = threadIdx.x;
   int lo = 0, hi = n0, PL = 1;
   if (t == 0) {
     g.set_level(0, 0);
@@ -66,81 +151,11 @@ __device__ int forest_levels(const ForestGrid& g, int n0, ForestSmem<BD, PI>& s)
   }
   while (lo < hi) {
     int run = hi;
-    for (int base = lo; base < hi; base += PI * BD) {
-      int cs[PI], ms[PI];
-#pragma unroll
-      for (int i = 0; i < PI; ++i) {
-        const int j = base + i * BD + t;
-        cs[i] = (j < hi) ? g.pq[j] : -1;
-      }
-      if (lo == 0) {
-#pragma unroll
-        for (int i = 0; i < PI; ++i) ms[i] = (cs[i] >= 0) ? g.pqm[base + i * BD + t] : 0;
-      } else {
-#pragma unroll
-        for (int i = 0; i < PI; ++i) ms[i] = (cs[i] >= 0) ? g.mask[cs[i]] : 0;
-#pragma unroll
-        for (int i = 0; i < PI; ++i)
-          if (cs[i] >= 0) g.pqm[base + i * BD + t] = (uint8_t)ms[i];
-      }
-      int pos_i[PI];
-#pragma unroll
-      for (int i = 0; i < PI; ++i) {
-        const int cnt = __popc(ms[i]);
-        int x = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, x, o);
-          if (lane >= o) x += y;
-        }
-        pos_i[i] = x - cnt;
-        if (lane == 31) s.chunk[i * W + w] = x;
-      }
-      __syncthreads();
-      if (w == 0) {
-        int v[PER], sum = 0;
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-          const int idx = lane * PER + q;
-          v[q] = (idx < C) ? s.chunk[idx] : 0;
-          sum += v[q];
-        }
-        int x = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, x, o);
-          if (lane >= o) x += y;
-        }
-        if (lane == 31) s.chunk_total = x;
-        int acc = x - sum;
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-          const int idx = lane * PER + q;
-          if (idx < C) s.chunk[idx] = acc;
-          acc += v[q];
-        }
-      }
-      __syncthreads();
-      const int tot = s.chunk_total;
-#pragma unroll
-      for (int i = 0; i < PI; ++i) pos_i[i] += run + s.chunk[i * W + w];
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < PI; ++i) {
-        int pos = pos_i[i];
-        const int parent = base + i * BD + t;
-        int msk = ms[i];
-        while (msk) {
-          const int k = __ffs(msk) - 1;
-          msk &= msk - 1;
-          g.pq[pos] = cs[i] + nbr_off(k, nx);
-          g.pqk[pos] = (uint8_t)(7 - k);
-          g.pqf[pos] = parent;
-          g.cntq[pos] = 1;
-          ++pos;
-        }
-      }
-      run += tot;
+    if (hi - lo <= BD) {
+      run += forest_round<BD, PI, 1>(g, s, lo, hi, lo, run);
+    } else {
+      for (int base = lo; base < hi; base += PI * BD)
+        run += forest_round<BD, PI, PI>(g, s, lo, hi, base, run);
     }
     __syncthreads();
     if (run == hi) break;
