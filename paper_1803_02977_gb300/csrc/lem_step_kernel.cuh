@@ -116,7 +116,14 @@ template <typename HT>
 __host__ __device__ constexpr int tile_h() {
   return sizeof(HT) == 4 ? 12 : 8;
 }
-constexpr int kWarpBytes = 7040;   // shared memory per warp for its forest
+// Shared memory per warp for its strip (Alg 1) and its forest (Algs 3-6).
+// 32 slices of 6016 B and the block's static state stay within a 196 KB
+// shared-memory carve-out, so 60 KB of the SM's 256 KB remain L1 (register
+// spills and the scattered mask and table loads of the warp tier hit there);
+// 7040 B slices needed the 228 KB carve-out and left 28 KB.  A multiple of
+// 128 B, so that every slice can take a TMA box.
+constexpr int kWarpBytes = 6016;
+static_assert(kWarpBytes % 128 == 0, "warp slices start 128-byte aligned");
 constexpr int kTileLv = 127;       // levels a warp forest may hold
 constexpr int kTileLvBytes = 256;  // its level offsets, u16 [0, kTileLv]
 // dynamic shared memory of the step kernel: the warps' forests, or (later in

@@ -468,8 +468,9 @@ __device__ __noinline__ int block_tier(const StepArgs<HT, CT>& a, Shared& s, int
 }
 
 // The warp tier of one step.  Work items (tiles, or halves of the last
-// tiles) are claimed from a device-wide counter; an item whose forest does
-// not fit a warp is appended to the device-wide overflow list ovf[] (counter
+// tiles) are claimed from a device-wide counter; a whole tile whose forest
+// does not fit a warp is retried as its two halves, and an item that still
+// does not fit is appended to the device-wide overflow list ovf[] (counter
 // *n_ovf) for the block tier.  The cells handled are added to *covered and
 // to the warp tier's total.
 template <typename HT, typename CT, bool kNewton>
@@ -523,18 +524,37 @@ __device__ __noinline__ void phase_tiles(const StepArgs<HT, CT>& a, Shared& s, i
   int item = 0;
   if (lane == 0) item = item_of(atomicAdd(tiles_next, 1));
   item = __shfl_sync(0xffffffffu, item, 0);
+  // pend: the second half of a split tile, run after the first; the next
+  // claim is taken once per claimed item (all warp-uniform)
+  int next = -1, pend = -1;
+  bool claimed = false;
   while (item >= 0) {
-    int next = 0;
-    if (lane == 0) next = item_of(atomicAdd(tiles_next, 1));
-    next = __shfl_sync(0xffffffffu, next, 0);
+    if (!claimed) {
+      int nc = 0;
+      if (lane == 0) nc = item_of(atomicAdd(tiles_next, 1));
+      next = __shfl_sync(0xffffffffu, nc, 0);
+      claimed = true;
+    }
     const int r = tile_forest(ta, q, s.off, item, lane);
     const int cur = item;
-    item = next;
     if (r >= 0) {
       mine += r;
+    } else if ((cur & 3) == 0) {
+      // a whole tile whose forest did not fit (nothing was written): its
+      // two halves hold fewer roots each and usually fit
+      item = cur | 1;
+      pend = cur | 2;
+      continue;
+    } else if (lane == 0) {
+      ovf[atomicAdd(n_ovf, 1)] = cur;
+    }
+    if (pend >= 0) {
+      item = pend;
+      pend = -1;
       continue;
     }
-    if (lane == 0) ovf[atomicAdd(n_ovf, 1)] = cur;
+    item = next;
+    claimed = false;
   }
   // per-warp totals (lane 0's count is the warp's)
   if (lane == 0) s.wcount[w] = (int)mine;
